@@ -1,0 +1,149 @@
+/*
+ * obfft.h -- C ABI of the GB300 Ozaki-Bailey FFT library (libobfft.so).
+ *
+ * The library computes full-FP64-accurate complex128 3-D FFTs as a Bailey
+ * six-step transform whose DFT stages are Ozaki-Scheme-II residue GEMMs on
+ * tensor cores (paper: "FP8 is All You Need (Part 2)", Algorithm 1), with the
+ * exact CRT reconstruction (Eq. fcrt, Eq. slicing, Algorithm 2) and one
+ * correctly rounded conversion per stage output.
+ *
+ * Conventions shared by every entry point
+ *  - Transform (Bailey paragraph of the Background; the sign is this
+ *    library's reading, the paper leaves it open):
+ *      forward  (dir = -1): Y[k] = sum_j X[j] exp(-2 pi i sum_a j_a k_a / n_a)
+ *      inverse  (dir = +1): the conjugate kernel, unnormalised (so the inverse
+ *               is also the adjoint of the forward transform).
+ *  - Layout: contiguous C-order [batch][n0][n1][n2] complex128, interleaved
+ *    (re, im) doubles, 16-byte aligned.  Axis 2 is transformed first, then 1,
+ *    then 0; each axis of length n = p * q uses the Bailey indices
+ *    j = j1 + p j2, k = k2 + q k1 with 1 <= p, q <= 64.
+ *  - Pointers passed to obfft_exec / obfft_exec_many are DEVICE pointers
+ *    (cudaMalloc'd or torch CUDA tensors) on the plan's device; the caller
+ *    owns them.  in == out is rejected (out-of-place only).
+ *  - Errors are returned as obfft_status, never by aborting; a thread-local
+ *    message is available from obfft_last_error().
+ *  - obfft_exec is asynchronous on `stream`.  One plan must not run on two
+ *    streams at the same time (it owns one scratch buffer).
+ */
+#ifndef OBFFT_H
+#define OBFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct obfft_plan_s *obfft_plan; /* opaque, owned by the library */
+
+typedef enum {
+    OBFFT_OK = 0,
+    OBFFT_ERR_ARG = 1,              /* bad pointer, size, direction or mode */
+    OBFFT_ERR_UNSUPPORTED_SIZE = 2, /* an axis does not factor as p*q, p,q <= 64 */
+    OBFFT_ERR_ALLOC = 3,            /* device or host allocation failed */
+    OBFFT_ERR_CUDA = 4,             /* a CUDA call failed (message has details) */
+    OBFFT_ERR_TIMEOUT = 5,          /* a device-side bounded wait gave up */
+    OBFFT_ERR_INTERNAL = 6
+} obfft_status;
+
+typedef enum {
+    /* residue GEMMs on tcgen05 FP8 E4M3 tensor cores (kind::f8f6f4), exact digit
+       planes; Phase A on tcgen05 FP16 */
+    OBFFT_MODE_FP8 = 0,
+    /* residue GEMMs on INT8 tensor cores through warp-level mma.sync s8 x s8
+       (the INT8 kind sm_103a accepts), two-limb residues */
+    OBFFT_MODE_INT8 = 1,
+    /* comparator: plain FP64 six-step FFT (radix butterflies + FP64 twiddles) */
+    OBFFT_MODE_FP64_NATIVE = 2
+} obfft_mode;
+
+/*
+ * Create a plan for `batch` grids of n0 x n1 x n2 (each n_a >= 1, and each
+ * n_a must factor as p*q with p, q <= 64, so n_a <= 4096).  Generates the
+ * quantised DFT and twiddle-fused matrices (Eq. twiddle-fusion, constants
+ * scaled by 2^52), their residue planes for the Rev-34 modulus set, the CRT
+ * constants (u_k byte slices, w_k, M) and allocates one device scratch buffer
+ * of the grid's size (paper: Algorithm 1 "Require" clause; Sec. tcgarner).
+ * The plan is bound to the CUDA device current at creation.
+ * Returns OBFFT_ERR_ARG for null `out` or non-positive sizes,
+ * OBFFT_ERR_UNSUPPORTED_SIZE for an axis that does not factor, OBFFT_ERR_ALLOC
+ * when device memory is short.
+ */
+obfft_status obfft_plan_create(obfft_plan *out, int64_t n0, int64_t n1, int64_t n2,
+                               int64_t batch, int mode);
+
+/*
+ * Run the transform: in/out are device pointers to batch*n0*n1*n2 complex128
+ * values (16-byte aligned, distinct buffers).  dir = -1 forward, +1 inverse.
+ * `stream` is a cudaStream_t (0 = legacy default stream).  Asynchronous:
+ * returns after enqueueing; kernel faults surface on a later synchronising
+ * call.  OBFFT_ERR_ARG for null/aliased/misaligned pointers or a bad dir.
+ */
+obfft_status obfft_exec(obfft_plan p, const void *in, void *out, int dir, void *stream);
+
+/* Release the plan's device tables and scratch.  NULL is accepted. */
+obfft_status obfft_destroy(obfft_plan p);
+
+/*
+ * Splits chosen for one axis (0, 1 or 2) of grid `grid` (0 for single-grid
+ * plans): n = (*p) * (*q).  The oracle takes them from here.
+ */
+obfft_status obfft_plan_get_splits(obfft_plan p, int grid, int axis, int *p_out, int *q_out);
+
+/*
+ * Plan for `count` independent grids of possibly different sizes
+ * (dims[g][0..2]) executed together (the uneven batch).  Same size rules as
+ * obfft_plan_create; the scratch is sized for the largest grid.
+ */
+obfft_status obfft_plan_create_many(obfft_plan *out, int count, const int64_t *dims /* [count][3] */,
+                                    int mode);
+
+/*
+ * Transform every grid of a _many plan: ins[g] / outs[g] are device pointers
+ * (arrays of `count` pointers in HOST memory).  Asynchronous on `stream`.
+ */
+obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, void *const *outs, int dir,
+                             void *stream);
+
+/*
+ * Run ONE Bailey stage of ONE axis pass on the current contents of `in`
+ * (debug / parity entry): stage 1 or 2 of the pass over axis `axis`.  `in`
+ * holds the pass input laid out [batch][A1][A2][n_axis] (axis contiguous),
+ * `out` receives:
+ *   stage 1: Y'[line][k2][j1] (complex128, lines x n_axis)
+ *   stage 2 (with in = the stage-1 output): the pass output, rotated to
+ *            [batch][n_axis][A1][A2].
+ * Grid sizes are those of the plan; A1, A2 are the other two axes in rotated
+ * order (pass over axis 2: A1 = n0, A2 = n1; axis 1: A1 = n2, A2 = n0;
+ * axis 0: A1 = n1, A2 = n2).
+ */
+obfft_status obfft_exec_stage(obfft_plan p, int axis, int stage, const void *in, void *out, int dir,
+                              void *stream);
+
+/*
+ * Host-only introspection (no GPU needed): the quantised constant
+ * RNE(2^52 exp(dir 2 pi i m / N)) the plans use (Bailey paragraph and
+ * Eq. twiddle-fusion: 53-bit signed significands, |re|, |im| <= 2^52), written
+ * to *re, *im.  OBFFT_ERR_ARG for N < 1 or null outputs.
+ */
+obfft_status obfft_host_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im);
+
+/*
+ * Host-only introspection of the CRT constants (Eq. fcrt, Eq. slicing, and the
+ * lift weights of Sec. "Exact Phase B"): moduli[12]; u_slices[12][15] = byte s
+ * of u_k (little-endian); w_slices[12][6] = byte t of w_k = round(2^48 u_k / M);
+ * M4[4] = M as little-endian 32-bit words.  Caller-owned host buffers.
+ */
+obfft_status obfft_host_crt_constants(uint32_t *moduli, uint8_t *u_slices, uint8_t *w_slices,
+                                      uint32_t *M4);
+
+/* Thread-local text of the last error (never NULL). */
+const char *obfft_last_error(void);
+
+/* Library version string. */
+const char *obfft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OBFFT_H */

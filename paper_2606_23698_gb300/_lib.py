@@ -1,0 +1,125 @@
+"""ctypes binding of libobfft.so: the C ABI of include/obfft.h, same names,
+argument marshalling only (every step of the transform runs in the library's
+CUDA kernels).  Loading fails loudly when the library is missing: there is no
+CPU fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libobfft.so")
+
+OBFFT_OK = 0
+OBFFT_ERR_ARG = 1
+OBFFT_ERR_UNSUPPORTED_SIZE = 2
+OBFFT_ERR_ALLOC = 3
+OBFFT_ERR_CUDA = 4
+OBFFT_ERR_TIMEOUT = 5
+OBFFT_ERR_INTERNAL = 6
+STATUS_NAMES = {0: "OBFFT_OK", 1: "OBFFT_ERR_ARG", 2: "OBFFT_ERR_UNSUPPORTED_SIZE",
+                3: "OBFFT_ERR_ALLOC", 4: "OBFFT_ERR_CUDA", 5: "OBFFT_ERR_TIMEOUT",
+                6: "OBFFT_ERR_INTERNAL"}
+
+OBFFT_MODE_FP8 = 0
+OBFFT_MODE_INT8 = 1
+OBFFT_MODE_FP64_NATIVE = 2
+MODES = {"fp8": OBFFT_MODE_FP8, "int8": OBFFT_MODE_INT8, "fp64": OBFFT_MODE_FP64_NATIVE}
+
+# every symbol include/obfft.h declares
+EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_splits",
+           "obfft_plan_create_many", "obfft_exec_many", "obfft_exec_stage", "obfft_last_error",
+           "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants")
+
+_lib = None
+
+
+class ObfftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libobfft.so not built ({path}); run __graft_entry__.build() or "
+                          "python paper_2606_23698_gb300/build.py")
+    L = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.obfft_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, i64, i64, i32]
+    L.obfft_plan_create_many.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i64), i32]
+    L.obfft_exec.argtypes = [vp, vp, vp, i32, vp]
+    L.obfft_exec_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp]
+    L.obfft_exec_stage.argtypes = [vp, i32, i32, vp, vp, i32, vp]
+    L.obfft_destroy.argtypes = [vp]
+    L.obfft_plan_get_splits.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    for f in ("obfft_plan_create", "obfft_plan_create_many", "obfft_exec", "obfft_exec_many",
+              "obfft_exec_stage", "obfft_destroy", "obfft_plan_get_splits"):
+        getattr(L, f).restype = i32
+    L.obfft_last_error.restype = ctypes.c_char_p
+    L.obfft_last_error.argtypes = []
+    L.obfft_version.restype = ctypes.c_char_p
+    L.obfft_version.argtypes = []
+    L.obfft_host_twiddle.argtypes = [i64, i64, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.obfft_host_twiddle.restype = i32
+    L.obfft_host_crt_constants.argtypes = [vp, vp, vp, vp]
+    L.obfft_host_crt_constants.restype = i32
+    _lib = L
+    return L
+
+
+def check(status: int) -> None:
+    if status != OBFFT_OK:
+        raise ObfftError(status, load().obfft_last_error().decode())
+
+
+# ---- thin same-name wrappers (argument marshalling only) --------------------
+def obfft_plan_create(n0: int, n1: int, n2: int, batch: int = 1, mode: int = OBFFT_MODE_FP8) -> int:
+    h = ctypes.c_void_p()
+    check(load().obfft_plan_create(ctypes.byref(h), n0, n1, n2, batch, mode))
+    return h.value
+
+
+def obfft_plan_create_many(dims, mode: int = OBFFT_MODE_FP8) -> int:
+    flat = [int(v) for d in dims for v in d]
+    arr = (ctypes.c_int64 * len(flat))(*flat)
+    h = ctypes.c_void_p()
+    check(load().obfft_plan_create_many(ctypes.byref(h), len(dims), arr, mode))
+    return h.value
+
+
+def obfft_exec(plan: int, in_ptr: int, out_ptr: int, dir: int, stream: int = 0) -> None:
+    check(load().obfft_exec(plan, in_ptr, out_ptr, dir, stream))
+
+
+def obfft_exec_many(plan: int, in_ptrs, out_ptrs, dir: int, stream: int = 0) -> None:
+    n = len(in_ptrs)
+    ins = (ctypes.c_void_p * n)(*in_ptrs)
+    outs = (ctypes.c_void_p * n)(*out_ptrs)
+    check(load().obfft_exec_many(plan, ins, outs, dir, stream))
+
+
+def obfft_exec_stage(plan: int, axis: int, stage: int, in_ptr: int, out_ptr: int, dir: int,
+                     stream: int = 0) -> None:
+    check(load().obfft_exec_stage(plan, axis, stage, in_ptr, out_ptr, dir, stream))
+
+
+def obfft_destroy(plan: int) -> None:
+    check(load().obfft_destroy(plan))
+
+
+def obfft_plan_get_splits(plan: int, grid: int, axis: int):
+    p, q = ctypes.c_int(), ctypes.c_int()
+    check(load().obfft_plan_get_splits(plan, grid, axis, ctypes.byref(p), ctypes.byref(q)))
+    return p.value, q.value
+
+
+def obfft_last_error() -> str:
+    return load().obfft_last_error().decode()
+
+
+def obfft_version() -> str:
+    return load().obfft_version().decode()

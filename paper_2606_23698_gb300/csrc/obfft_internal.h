@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's host and device translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "obfft.h"
+
+namespace obfft {
+
+constexpr int NMOD = 12;     // r = 12 moduli (Rev-34 set)
+constexpr int S_RAW = 15;    // byte slices of the CRT idempotents (Eq. slicing)
+constexpr int S_FRAC = 6;    // byte slices of the 48-bit lift weights
+constexpr int KMAX = 64;     // largest Bailey factor p or q
+constexpr int CT_COLS = 32;  // columns per CTA of the INT8 stage kernel
+
+// Rev-34 modulus set (Background, Ozaki Scheme II paragraph).
+extern const int kModuli[NMOD];
+
+// Per-modulus constants used on the device (one copy in __constant__ memory).
+struct ModConsts {
+    uint32_t m[NMOD];         // moduli
+    uint32_t barrett[NMOD];   // floor(2^32 / m)
+    uint32_t off27[NMOD];     // smallest multiple of m >= 2^27 (makes |x| < 2^27 non-negative)
+    uint32_t c20[NMOD];       // 2^20 mod m
+    uint32_t c40[NMOD];       // 2^40 mod m
+    uint32_t c55neg[NMOD];    // (-2^55) mod m : removes the +2^55 bias of deconstructed integers
+    uint32_t u32[NMOD][4];    // u_k as four little-endian 32-bit words (u_k < M < 2^118)
+    float yk_over_mk[NMOD];   // u_k / M = y_k / m_k rounded to float (lift quotient estimate)
+    uint32_t M32[4];          // M
+    uint32_t halfM32[4];      // M / 2 (M is even)
+    uint8_t us[NMOD][S_RAW];  // byte slices of u_k (Phase A B-matrix)
+    uint8_t ws[NMOD][S_FRAC]; // byte slices of w_k = round(2^48 u_k / M)
+};
+
+// Host-side constant generation (plan.cpp).
+void make_mod_consts(ModConsts *mc);
+// RNE(2^52 * cos / sin(2 pi m / N)) with the sign of the imaginary part
+// chosen by dir (-1: exp(-i theta)); returns false on internal inconsistency.
+void quantised_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im);
+
+// One axis of a grid: n = p * q.
+struct AxisPlan {
+    int n = 1, p = 1, q = 1;
+};
+
+// Device tables for one (n, p, q, dir, mode) axis.
+struct AxisTables {
+    int n = 0, p = 0, q = 0, dir = 0;
+    // INT8 mode: fragment-native s8 limb tables, stage 1 (1 group) / stage 2 (q groups)
+    void *int8_s1 = nullptr, *int8_s2 = nullptr;
+    size_t int8_s1_bytes = 0, int8_s2_bytes = 0;
+    // FP64 native comparator: twiddles exp(dir 2 pi i m / n) for m < n as double pairs
+    double *tw = nullptr;
+    // quantised int64 constants (kept for the FP8 path and for debugging)
+    std::vector<int64_t> Fq, Fp;  // [q][q][2], [q][p][p][2]
+};
+
+struct GridDesc {
+    int64_t n[3];
+    AxisPlan ax[3];
+};
+
+}  // namespace obfft
+
+struct obfft_plan_s {
+    int mode = 0;
+    int device = 0;
+    int64_t batch = 1;
+    std::vector<obfft::GridDesc> grids;   // one for create, count for create_many
+    std::vector<obfft::AxisTables> tables;  // one per distinct (n, dir)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    obfft::ModConsts *d_consts = nullptr;
+};
+
+namespace obfft {
+// error reporting
+obfft_status set_error(obfft_status st, const std::string &msg);
+AxisTables *get_tables(obfft_plan p, int n, int pp, int qq, int dir);
+
+// Launchers (one CUDA translation unit each).
+// Stage geometry: `lines` lines of length n = p*q per batch-slice structure.
+struct StageGeom {
+    int64_t L;       // total lines = batch * P
+    int64_t P;       // lines per batch item (A1 * A2)
+    int n, p, q;
+};
+cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const StageGeom &g,
+                              int stage, const double2 *in, double2 *out, cudaStream_t s);
+cudaError_t launch_stage_fp64(const AxisTables &t, const StageGeom &g, int stage,
+                              const double2 *in, double2 *out, cudaStream_t s);
+}  // namespace obfft

@@ -1,0 +1,562 @@
+// Host side of libobfft: constant generation, plan creation and the C ABI.
+//
+// Constants (all computed here, independently of any test code):
+//   * moduli, M = prod m_k, CRT idempotents u_k = (M/m_k) y_k with
+//     y_k = (M/m_k)^-1 mod m_k (Eq. fcrt), their byte slices (Eq. slicing),
+//     lift weights w_k = round(2^48 u_k / M) = round(2^48 y_k / m_k).
+//   * quantised DFT / twiddle-fused matrices RNE(2^52 omega) (Bailey
+//     paragraph, Eq. twiddle-fusion), from double-double sin/cos with an exact
+//     octant reduction of the rational angle m / N.
+//   * INT8-mode limb tables in the register order of mma.m16n8k32 A fragments.
+//   * FP64-comparator twiddle tables.
+// Build flag: this file relies on separately rounded double operations
+// (compile with -ffp-contract=off).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "obfft_internal.h"
+
+namespace obfft {
+
+const int kModuli[NMOD] = {2039, 2029, 2027, 1089, 1024, 961, 841, 625, 529, 511, 491, 487};
+
+static thread_local std::string g_last_error = "no error";
+
+obfft_status set_error(obfft_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------ modular helpers
+static int64_t inv_mod(int64_t a, int64_t m) {
+    int64_t t = 0, newt = 1, r = m, newr = ((a % m) + m) % m;
+    while (newr) {
+        int64_t qq = r / newr, tmp;
+        tmp = t - qq * newt; t = newt; newt = tmp;
+        tmp = r - qq * newr; r = newr; newr = tmp;
+    }
+    return t < 0 ? t + m : t;
+}
+static int64_t pow2_mod(int e, int64_t m) {
+    int64_t r = 1 % m;
+    for (int i = 0; i < e; i++) r = (r * 2) % m;
+    return r;
+}
+
+void make_mod_consts(ModConsts *mc) {
+    memset(mc, 0, sizeof(*mc));
+    u128 M = 1;
+    for (int k = 0; k < NMOD; k++) M *= (u128)kModuli[k];
+    for (int k = 0; k < NMOD; k++) {
+        uint32_t m = (uint32_t)kModuli[k];
+        mc->m[k] = m;
+        mc->barrett[k] = (uint32_t)((1ull << 32) / m);
+        mc->off27[k] = (uint32_t)((((1ull << 27) + m - 1) / m) * m);
+        mc->c20[k] = (uint32_t)pow2_mod(20, m);
+        mc->c40[k] = (uint32_t)pow2_mod(40, m);
+        mc->c55neg[k] = (uint32_t)((m - pow2_mod(55, m)) % m);
+        u128 Mk = M / m;
+        int64_t y = inv_mod((int64_t)(Mk % m), m);
+        u128 u = Mk * (u128)y;  // < M < 2^118
+        for (int w = 0; w < 4; w++) mc->u32[k][w] = (uint32_t)(u >> (32 * w));
+        for (int s = 0; s < S_RAW; s++) mc->us[k][s] = (uint8_t)(u >> (8 * s));
+        // w_k = floor(2^48 y_k / m_k + 1/2) = floor((2^49 y_k + m_k) / (2 m_k))
+        u128 wk = (((u128)y << 49) + m) / ((u128)2 * m);
+        for (int t = 0; t < S_FRAC; t++) mc->ws[k][t] = (uint8_t)(wk >> (8 * t));
+        mc->yk_over_mk[k] = (float)((double)y / (double)m);
+    }
+    for (int w = 0; w < 4; w++) {
+        mc->M32[w] = (uint32_t)(M >> (32 * w));
+        mc->halfM32[w] = (uint32_t)((M >> 1) >> (32 * w));
+    }
+}
+
+// --------------------------------------------------- double-double sin / cos
+struct dd { double hi, lo; };
+static dd two_sum(double a, double b) {
+    double s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+static dd qts(double a, double b) {
+    double s = a + b;
+    return {s, b - (s - a)};
+}
+static dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = qts(s.hi, s.lo);
+    s.lo += t.lo;
+    return qts(s.hi, s.lo);
+}
+static dd dd_mul(dd a, dd b) {
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+    return qts(p, e);
+}
+static dd dd_div_int(dd a, double d) {  // a / d for an exactly representable d
+    double q1 = a.hi / d;
+    dd prod = {q1 * d, fma(q1, d, -q1 * d)};
+    dd r = dd_add(a, {-prod.hi, -prod.lo});
+    double q2 = r.hi / d;
+    return qts(q1, q2);
+}
+static const dd DD_PI = {3.141592653589793116, 1.2246467991473532e-16};
+
+// cos and sin of phi = pi * num / den, |num / den| <= 1/4
+static void dd_cos_sin(int64_t num, int64_t den, dd *c, dd *s) {
+    dd r = dd_div_int({(double)num, 0.0}, (double)den);
+    dd phi = dd_mul(DD_PI, r);
+    dd phi2 = dd_mul(phi, phi);
+    dd cs = {1.0, 0.0}, sn = phi;
+    dd term = {1.0, 0.0};
+    for (int n = 1; n < 30; n++) {  // cos: term_n = -term_{n-1} phi^2 / ((2n-1)(2n))
+        term = dd_div_int(dd_mul(term, phi2), (double)((2 * n - 1) * (2 * n)));
+        term = {-term.hi, -term.lo};
+        cs = dd_add(cs, term);
+    }
+    term = phi;
+    for (int n = 1; n < 30; n++) {
+        term = dd_div_int(dd_mul(term, phi2), (double)((2 * n) * (2 * n + 1)));
+        term = {-term.hi, -term.lo};
+        sn = dd_add(sn, term);
+    }
+    *c = cs;
+    *s = sn;
+}
+
+// cos / sin (2 pi m / N) with exact reduction to |phi| <= pi/4
+static void dd_cos_sin_2pi(int64_t m, int64_t N, dd *c, dd *s) {
+    m %= N;
+    if (m < 0) m += N;
+    int64_t k = (8 * m + N) / (2 * N);  // round(4 m / N)
+    int64_t num = 4 * m - k * N;        // phi = pi num / (2N)
+    dd cc, ss;
+    if (num == 0) {
+        cc = {1.0, 0.0};
+        ss = {0.0, 0.0};
+    } else {
+        dd_cos_sin(num, 2 * N, &cc, &ss);
+    }
+    switch (k % 4) {
+        case 0: *c = cc; *s = ss; break;
+        case 1: *c = {-ss.hi, -ss.lo}; *s = cc; break;
+        case 2: *c = {-cc.hi, -cc.lo}; *s = {-ss.hi, -ss.lo}; break;
+        default: *c = ss; *s = {-cc.hi, -cc.lo}; break;
+    }
+}
+
+static int64_t rne_dd_times_2p52(dd v) {
+    double hi = ldexp(v.hi, 52), lo = ldexp(v.lo, 52);
+    double n = rint(hi);
+    double d = (hi - n) + lo;  // hi - n exact
+    if (d > 0.5) n += 1.0;
+    else if (d < -0.5) n -= 1.0;
+    else if (d == 0.5 || d == -0.5) {
+        double cand = d > 0 ? n + 1.0 : n - 1.0;
+        if (fmod(cand, 2.0) == 0.0) n = cand;
+    }
+    return (int64_t)n;
+}
+
+void quantised_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im) {
+    dd c, s;
+    dd_cos_sin_2pi(m, N, &c, &s);
+    *re = rne_dd_times_2p52(c);
+    int64_t si = rne_dd_times_2p52(s);
+    *im = dir < 0 ? -si : si;
+}
+
+// ------------------------------------------------------------ table building
+static inline int64_t modc(int64_t x, int64_t m) {
+    int64_t r = x % m;
+    return r < 0 ? r + m : r;
+}
+
+// INT8 limb table for one stage.  F: [groups][Kout][K][2] int64, K == Kout.
+// Output layout [g][mod][prod][mt][part][kb][lane] uint4 (16 bytes each).
+static std::vector<uint32_t> build_int8_table(const std::vector<int64_t> &F, int groups, int K) {
+    const int KPAD = K <= 32 ? 32 : 64;
+    const int KB2 = 2 * KPAD / 32;
+    const int MT = (K + 15) / 16;
+    std::vector<uint32_t> out((size_t)groups * NMOD * 3 * MT * 2 * KB2 * 32 * 4, 0u);
+    std::vector<int32_t> limb[2];  // [row 16*MT][2*KPAD] per part
+    for (int g = 0; g < groups; g++)
+        for (int k = 0; k < NMOD; k++) {
+            const int64_t m = kModuli[k];
+            for (int pd = 0; pd < 3; pd++) {
+                limb[0].assign((size_t)16 * MT * 2 * KPAD, 0);
+                limb[1].assign((size_t)16 * MT * 2 * KPAD, 0);
+                for (int r = 0; r < K; r++)
+                    for (int j = 0; j < K; j++) {
+                        const int64_t *e = &F[(((size_t)g * K + r) * K + j) * 2];
+                        int64_t a = pd == 0 ? e[0] : pd == 1 ? e[1] : e[0] + e[1];
+                        int64_t G = modc(a, m), H = (256 * G) % m;
+                        int64_t vals[2] = {G, H};
+                        for (int gh = 0; gh < 2; gh++) {
+                            int64_t v = vals[gh];
+                            int64_t hi = (v + 128) >> 8, lo = v - 256 * hi;  // lo in [-128,127], hi in [0,8]
+                            size_t col = (size_t)gh * KPAD + j;
+                            limb[0][(size_t)r * 2 * KPAD + col] = (int32_t)lo;
+                            limb[1][(size_t)r * 2 * KPAD + col] = (int32_t)hi;
+                        }
+                    }
+                for (int mt = 0; mt < MT; mt++)
+                    for (int part = 0; part < 2; part++)
+                        for (int kb = 0; kb < KB2; kb++)
+                            for (int lane = 0; lane < 32; lane++) {
+                                size_t idx = ((((((size_t)g * NMOD + k) * 3 + pd) * MT + mt) * 2 + part) * KB2 + kb) * 32 + lane;
+                                for (int reg = 0; reg < 4; reg++) {
+                                    int row = mt * 16 + (lane >> 2) + ((reg & 1) ? 8 : 0);
+                                    int kc = kb * 32 + 4 * (lane & 3) + ((reg & 2) ? 16 : 0);
+                                    uint32_t word = 0;
+                                    for (int b = 0; b < 4; b++) {
+                                        int32_t v = limb[part][(size_t)row * 2 * KPAD + kc + b];
+                                        word |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
+                                    }
+                                    out[idx * 4 + reg] = word;
+                                }
+                            }
+            }
+        }
+    return out;
+}
+
+static void fill_matrices(AxisTables &t) {
+    const int p = t.p, q = t.q, n = t.n, dir = t.dir;
+    t.Fq.assign((size_t)q * q * 2, 0);
+    for (int k2 = 0; k2 < q; k2++)
+        for (int j2 = 0; j2 < q; j2++)
+            quantised_twiddle((int64_t)j2 * k2 % q, q, dir, &t.Fq[((size_t)k2 * q + j2) * 2],
+                              &t.Fq[((size_t)k2 * q + j2) * 2 + 1]);
+    t.Fp.assign((size_t)q * p * p * 2, 0);
+    for (int k2 = 0; k2 < q; k2++)
+        for (int k1 = 0; k1 < p; k1++)
+            for (int j1 = 0; j1 < p; j1++) {
+                int64_t e = ((int64_t)j1 * ((int64_t)q * k1 + k2)) % n;
+                size_t idx = (((size_t)k2 * p + k1) * p + j1) * 2;
+                quantised_twiddle(e, n, dir, &t.Fp[idx], &t.Fp[idx + 1]);
+            }
+}
+
+static cudaError_t upload(const void *host, size_t bytes, void **dev) {
+    cudaError_t e = cudaMalloc(dev, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice);
+}
+
+static obfft_status build_tables(obfft_plan P, AxisTables &t) {
+    fill_matrices(t);
+    cudaError_t e = cudaSuccess;
+    if (P->mode == OBFFT_MODE_INT8) {
+        std::vector<uint32_t> s1 = build_int8_table(t.Fq, 1, t.q);
+        std::vector<uint32_t> s2 = build_int8_table(t.Fp, t.q, t.p);
+        t.int8_s1_bytes = s1.size() * 4;
+        t.int8_s2_bytes = s2.size() * 4;
+        e = upload(s1.data(), t.int8_s1_bytes, &t.int8_s1);
+        if (e == cudaSuccess) e = upload(s2.data(), t.int8_s2_bytes, &t.int8_s2);
+    } else if (P->mode == OBFFT_MODE_FP64_NATIVE) {
+        std::vector<double> tw;
+        auto push = [&](int N) {
+            for (int m = 0; m < N; m++) {
+                dd c, s;
+                dd_cos_sin_2pi(m, N, &c, &s);
+                tw.push_back(c.hi);
+                tw.push_back(t.dir < 0 ? -s.hi : s.hi);
+            }
+        };
+        push(t.n);
+        push(t.q);
+        push(t.p);
+        e = upload(tw.data(), tw.size() * sizeof(double), (void **)&t.tw);
+    } else {
+        return set_error(OBFFT_ERR_UNSUPPORTED_SIZE, "mode not available in this build");
+    }
+    if (e != cudaSuccess) return set_error(OBFFT_ERR_ALLOC, std::string("table upload: ") + cudaGetErrorString(e));
+    return OBFFT_OK;
+}
+
+AxisTables *get_tables(obfft_plan P, int n, int pp, int qq, int dir) {
+    for (auto &t : P->tables)
+        if (t.n == n && t.p == pp && t.q == qq && t.dir == dir) return &t;
+    return nullptr;
+}
+
+// Bailey split: q = smallest divisor >= sqrt(n), p = n / q; both <= 64.
+static bool choose_split(int64_t n, AxisPlan *a) {
+    if (n == 1) {
+        a->n = 1; a->p = 1; a->q = 1;
+        return true;
+    }
+    for (int64_t q = 1; q <= n; q++)
+        if (n % q == 0 && q * q >= n) {
+            int64_t p = n / q;
+            if (p > KMAX || q > KMAX) return false;
+            a->n = (int)n; a->p = (int)p; a->q = (int)q;
+            return true;
+        }
+    return false;
+}
+
+static void free_tables(obfft_plan P) {
+    for (auto &t : P->tables) {
+        cudaFree(t.int8_s1);
+        cudaFree(t.int8_s2);
+        cudaFree(t.tw);
+    }
+    P->tables.clear();
+}
+
+}  // namespace obfft
+
+using namespace obfft;
+
+static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
+    // tables for both directions of every distinct axis
+    for (auto &gd : P->grids)
+        for (int a = 0; a < 3; a++) {
+            const AxisPlan &ap = gd.ax[a];
+            if (ap.n == 1) continue;
+            for (int dir : {-1, 1}) {
+                if (get_tables(P, ap.n, ap.p, ap.q, dir)) continue;
+                AxisTables t;
+                t.n = ap.n; t.p = ap.p; t.q = ap.q; t.dir = dir;
+                P->tables.push_back(t);
+                obfft_status st = build_tables(P, P->tables.back());
+                if (st != OBFFT_OK) {
+                    free_tables(P);
+                    cudaFree(P->d_consts);
+                    delete P;
+                    return st;
+                }
+            }
+        }
+    size_t maxel = 0;
+    for (auto &gd : P->grids) maxel = std::max(maxel, (size_t)(gd.n[0] * gd.n[1] * gd.n[2]));
+    P->scratch_bytes = maxel * (size_t)P->batch * 16;
+    cudaError_t e = cudaMalloc(&P->scratch, P->scratch_bytes ? P->scratch_bytes : 16);
+    if (e != cudaSuccess) {
+        free_tables(P);
+        cudaFree(P->d_consts);
+        delete P;
+        return set_error(OBFFT_ERR_ALLOC, std::string("scratch: ") + cudaGetErrorString(e));
+    }
+    *out = P;
+    return OBFFT_OK;
+}
+
+static obfft_status new_plan(int mode, obfft_plan *P) {
+    if (mode != OBFFT_MODE_FP8 && mode != OBFFT_MODE_INT8 && mode != OBFFT_MODE_FP64_NATIVE)
+        return set_error(OBFFT_ERR_ARG, "unknown mode");
+    obfft_plan p = new obfft_plan_s();
+    p->mode = mode;
+    cudaGetDevice(&p->device);
+    ModConsts mc;
+    make_mod_consts(&mc);
+    cudaError_t e = upload(&mc, sizeof(mc), (void **)&p->d_consts);
+    if (e != cudaSuccess) {
+        delete p;
+        return set_error(OBFFT_ERR_ALLOC, std::string("constants: ") + cudaGetErrorString(e));
+    }
+    *P = p;
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_plan_create(obfft_plan *out, int64_t n0, int64_t n1, int64_t n2,
+                                          int64_t batch, int mode) {
+    if (!out) return set_error(OBFFT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n0 < 1 || n1 < 1 || n2 < 1 || batch < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
+    GridDesc gd;
+    gd.n[0] = n0; gd.n[1] = n1; gd.n[2] = n2;
+    for (int a = 0; a < 3; a++)
+        if (!choose_split(gd.n[a], &gd.ax[a]))
+            return set_error(OBFFT_ERR_UNSUPPORTED_SIZE,
+                             "axis " + std::to_string(a) + " of length " + std::to_string(gd.n[a]) +
+                                 " does not factor as p*q with p, q <= 64");
+    obfft_plan P;
+    obfft_status st = new_plan(mode, &P);
+    if (st != OBFFT_OK) return st;
+    P->batch = batch;
+    P->grids.push_back(gd);
+    return finish_create(P, out);
+}
+
+extern "C" obfft_status obfft_plan_create_many(obfft_plan *out, int count, const int64_t *dims, int mode) {
+    if (!out) return set_error(OBFFT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !dims) return set_error(OBFFT_ERR_ARG, "count must be >= 1 and dims non-NULL");
+    std::vector<GridDesc> grids;
+    for (int g = 0; g < count; g++) {
+        GridDesc gd;
+        for (int a = 0; a < 3; a++) {
+            gd.n[a] = dims[g * 3 + a];
+            if (gd.n[a] < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
+            if (!choose_split(gd.n[a], &gd.ax[a]))
+                return set_error(OBFFT_ERR_UNSUPPORTED_SIZE, "axis length " + std::to_string(gd.n[a]) +
+                                                                 " does not factor as p*q with p, q <= 64");
+        }
+        grids.push_back(gd);
+    }
+    obfft_plan P;
+    obfft_status st = new_plan(mode, &P);
+    if (st != OBFFT_OK) return st;
+    P->grids = grids;
+    return finish_create(P, out);
+}
+
+extern "C" obfft_status obfft_destroy(obfft_plan p) {
+    if (!p) return OBFFT_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    free_tables(p);
+    cudaFree(p->scratch);
+    cudaFree(p->d_consts);
+    cudaSetDevice(cur);
+    delete p;
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_plan_get_splits(obfft_plan p, int grid, int axis, int *p_out, int *q_out) {
+    if (!p || !p_out || !q_out || axis < 0 || axis > 2 || grid < 0 || grid >= (int)p->grids.size())
+        return set_error(OBFFT_ERR_ARG, "bad plan, grid, axis or output pointer");
+    *p_out = p->grids[grid].ax[axis].p;
+    *q_out = p->grids[grid].ax[axis].q;
+    return OBFFT_OK;
+}
+
+// geometry of the pass over `axis` (0, 1, 2) of grid gd: lines, lines per batch item
+static StageGeom pass_geom(const GridDesc &gd, int64_t batch, int axis) {
+    StageGeom g;
+    const AxisPlan &ap = gd.ax[axis];
+    int64_t tot = gd.n[0] * gd.n[1] * gd.n[2];
+    g.P = tot / gd.n[axis];
+    g.L = g.P * batch;
+    g.n = ap.n; g.p = ap.p; g.q = ap.q;
+    return g;
+}
+
+static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, int axis, int stage,
+                              const double2 *in, double2 *out, int dir, cudaStream_t s) {
+    const AxisPlan &ap = gd.ax[axis];
+    AxisTables *t = get_tables(P, ap.n, ap.p, ap.q, dir);
+    if (!t) return set_error(OBFFT_ERR_INTERNAL, "missing tables");
+    StageGeom g = pass_geom(gd, batch, axis);
+    cudaError_t e;
+    if (P->mode == OBFFT_MODE_INT8)
+        e = launch_stage_int8(*t, P->d_consts, g, stage, in, out, s);
+    else if (P->mode == OBFFT_MODE_FP64_NATIVE)
+        e = launch_stage_fp64(*t, g, stage, in, out, s);
+    else
+        return set_error(OBFFT_ERR_ARG, "mode not available in this build");
+    if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    return OBFFT_OK;
+}
+
+static obfft_status exec_grid(obfft_plan P, const GridDesc &gd, int64_t batch, const double2 *in,
+                              double2 *out, int dir, cudaStream_t s) {
+    const double2 *src = in;
+    double2 *scratch = (double2 *)P->scratch;
+    const int64_t total = gd.n[0] * gd.n[1] * gd.n[2] * batch;
+    for (int axis = 2; axis >= 0; axis--) {
+        const AxisPlan &ap = gd.ax[axis];
+        if (ap.n == 1) {
+            // length-1 axis: identity; the axis rotation [B][A1][A2][1] -> [B][1][A1][A2]
+            // leaves the memory order unchanged
+            if (src != out) {
+                cudaError_t e = cudaMemcpyAsync(out, src, total * 16, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
+            }
+        } else {
+            obfft_status st = run_stage(P, gd, batch, axis, 1, src, scratch, dir, s);
+            if (st != OBFFT_OK) return st;
+            st = run_stage(P, gd, batch, axis, 2, scratch, out, dir, s);
+            if (st != OBFFT_OK) return st;
+        }
+        src = out;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
+    return OBFFT_OK;
+}
+
+static obfft_status check_ptrs(const void *in, void *out) {
+    if (!in || !out) return set_error(OBFFT_ERR_ARG, "in/out is NULL");
+    if (in == out) return set_error(OBFFT_ERR_ARG, "in == out: out-of-place only");
+    if (((uintptr_t)in | (uintptr_t)out) & 15) return set_error(OBFFT_ERR_ARG, "in/out must be 16-byte aligned");
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_exec(obfft_plan p, const void *in, void *out, int dir, void *stream) {
+    if (!p) return set_error(OBFFT_ERR_ARG, "plan is NULL");
+    if (dir != -1 && dir != 1) return set_error(OBFFT_ERR_ARG, "dir must be -1 or +1");
+    obfft_status st = check_ptrs(in, out);
+    if (st != OBFFT_OK) return st;
+    if (p->grids.size() != 1) return set_error(OBFFT_ERR_ARG, "plan has several grids: use obfft_exec_many");
+    // the ranges must not overlap
+    size_t bytes = (size_t)(p->grids[0].n[0] * p->grids[0].n[1] * p->grids[0].n[2] * p->batch) * 16;
+    uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+    if (a < b + bytes && b < a + bytes) return set_error(OBFFT_ERR_ARG, "in and out overlap");
+    return exec_grid(p, p->grids[0], p->batch, (const double2 *)in, (double2 *)out, dir, (cudaStream_t)stream);
+}
+
+extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, void *const *outs, int dir,
+                                        void *stream) {
+    if (!p || !ins || !outs) return set_error(OBFFT_ERR_ARG, "NULL argument");
+    if (dir != -1 && dir != 1) return set_error(OBFFT_ERR_ARG, "dir must be -1 or +1");
+    for (size_t g = 0; g < p->grids.size(); g++) {
+        obfft_status st = check_ptrs(ins[g], outs[g]);
+        if (st != OBFFT_OK) return st;
+    }
+    for (size_t g = 0; g < p->grids.size(); g++) {
+        obfft_status st = exec_grid(p, p->grids[g], 1, (const double2 *)ins[g], (double2 *)outs[g], dir,
+                                    (cudaStream_t)stream);
+        if (st != OBFFT_OK) return st;
+    }
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_exec_stage(obfft_plan p, int axis, int stage, const void *in, void *out, int dir,
+                                         void *stream) {
+    if (!p || axis < 0 || axis > 2 || (stage != 1 && stage != 2)) return set_error(OBFFT_ERR_ARG, "bad argument");
+    if (dir != -1 && dir != 1) return set_error(OBFFT_ERR_ARG, "dir must be -1 or +1");
+    obfft_status st = check_ptrs(in, out);
+    if (st != OBFFT_OK) return st;
+    if (p->grids[0].ax[axis].n == 1) return set_error(OBFFT_ERR_ARG, "axis of length 1 has no stages");
+    st = run_stage(p, p->grids[0], p->batch, axis, stage, (const double2 *)in, (double2 *)out, dir,
+                   (cudaStream_t)stream);
+    return st;
+}
+
+extern "C" obfft_status obfft_host_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im) {
+    if (N < 1 || !re || !im) return set_error(OBFFT_ERR_ARG, "bad argument");
+    quantised_twiddle(m, N, dir, re, im);
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_host_crt_constants(uint32_t *moduli, uint8_t *u_slices, uint8_t *w_slices,
+                                                 uint32_t *M4) {
+    if (!moduli || !u_slices || !w_slices || !M4) return set_error(OBFFT_ERR_ARG, "NULL output");
+    ModConsts mc;
+    make_mod_consts(&mc);
+    for (int k = 0; k < NMOD; k++) {
+        moduli[k] = mc.m[k];
+        for (int s = 0; s < S_RAW; s++) u_slices[k * S_RAW + s] = mc.us[k][s];
+        for (int t = 0; t < S_FRAC; t++) w_slices[k * S_FRAC + t] = mc.ws[k][t];
+    }
+    for (int w = 0; w < 4; w++) M4[w] = mc.M32[w];
+    return OBFFT_OK;
+}
+
+extern "C" const char *obfft_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *obfft_version(void) { return "obfft 0.1 (sm_103a)"; }

@@ -1,0 +1,73 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and validates arguments without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    syms = []
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", name)).read()
+            syms += re.findall(r"^[a-z_ ]*?\*?\s*\b(obfft_[a-z_0-9]+)\s*\(", txt, re.M)
+    return sorted(set(syms))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_23698_gb300 import _lib
+    from paper_2606_23698_gb300 import build as B
+    B.build()
+    return _lib.load()
+
+
+def test_header_symbols_exported(lib):
+    syms = header_symbols()
+    assert "obfft_plan_create" in syms and "obfft_exec" in syms and "obfft_destroy" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_binding_names_match_header():
+    from paper_2606_23698_gb300 import _lib
+    assert set(_lib.EXPORTS) == set(header_symbols())
+
+
+def test_argument_validation(lib):
+    h = ctypes.c_void_p()
+    assert lib.obfft_plan_create(ctypes.byref(h), 0, 4, 4, 1, 1) == 1
+    assert lib.obfft_plan_create(None, 4, 4, 4, 1, 1) == 1
+    assert lib.obfft_plan_create(ctypes.byref(h), 4, 4, 4, 1, 7) == 1       # bad mode
+    assert lib.obfft_plan_create(ctypes.byref(h), 4, 4, 134, 1, 1) == 2     # 134 = 2 * 67
+    assert lib.obfft_plan_create(ctypes.byref(h), 4, 4, 8192, 1, 1) == 2    # > 64 * 64
+    assert b"factor" in lib.obfft_last_error()
+    assert lib.obfft_exec(None, None, None, -1, None) == 1
+    assert lib.obfft_destroy(None) == 0
+    assert lib.obfft_exec_many(None, None, None, -1, None) == 1
+
+
+def test_host_constants_match_oracle(lib):
+    """The library's own constant generator agrees with the oracle's big-integer
+    definitions bit for bit (quantised twiddles, CRT slices, lift weights, M)."""
+    from oracle import constants as C
+    re_, im_ = ctypes.c_int64(), ctypes.c_int64()
+    for N in (8, 12, 16, 24, 32, 64, 96, 128, 192, 384, 1024, 4096):
+        step = max(1, N // 97)
+        for m in range(0, N, step):
+            for d in (-1, 1):
+                assert lib.obfft_host_twiddle(m, N, d, ctypes.byref(re_), ctypes.byref(im_)) == 0
+                assert (re_.value, im_.value) == C.quantised_twiddle(m, N, d), (m, N, d)
+    mods = (ctypes.c_uint32 * 12)()
+    us = (ctypes.c_uint8 * 180)()
+    ws = (ctypes.c_uint8 * 72)()
+    M4 = (ctypes.c_uint32 * 4)()
+    assert lib.obfft_host_crt_constants(mods, us, ws, M4) == 0
+    assert list(mods) == list(C.MODULI)
+    assert [list(us[15 * k:15 * k + 15]) for k in range(12)] == C.U_SLICES
+    assert [list(ws[6 * k:6 * k + 6]) for k in range(12)] == C.W_SLICES
+    assert sum(int(M4[i]) << (32 * i) for i in range(4)) == C.M

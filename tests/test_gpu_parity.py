@@ -1,0 +1,180 @@
+"""GPU parity: the CUDA path against the oracle through the C ABI.
+
+Bit-exact: the Ozaki modes reach the exact integer sum_j F~ x~ per stage and
+round once, so every output double must equal the oracle's.  Accuracy: the
+FP64-native comparator and the Ozaki modes against double-double."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ref
+from synth import inputs as S
+from tests.helpers import bits_equal, mismatch_report, oracle_full
+
+pytestmark = pytest.mark.gpu
+
+OZAKI_MODES = ["int8"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2606_23698_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available()
+
+
+def plan(shape, mode, batch=1):
+    from paper_2606_23698_gb300 import Plan
+    return Plan(*shape, batch=batch, mode=mode)
+
+
+def splits_of(pl):
+    return tuple(pl.splits(a) for a in range(3))
+
+
+def run(pl, x_host, dir=-1):
+    x = torch.from_numpy(np.ascontiguousarray(x_host)).cuda()
+    y = pl.exec(x, dir=dir)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", OZAKI_MODES)
+@pytest.mark.parametrize("shape", [(8, 8, 8), (4, 12, 16), (2, 32, 5), (16, 16, 16), (1, 1, 64)])
+def test_small_grids_bit_exact(mode, shape):
+    x = S.complex_uniform(S.SEED_64, shape).numpy()
+    pl = plan(shape, mode)
+    y = run(pl, x)
+    ref_ = oracle_full(x, splits_of(pl), -1)
+    assert bits_equal(y, ref_), mismatch_report(y, ref_)
+
+
+@pytest.mark.parametrize("mode", OZAKI_MODES)
+def test_64cube_forward_bit_exact_and_accurate(mode):
+    """64^3, splits 8 x 8, uniform[-1,1) re/im: bit-exact vs the oracle and
+    within 1e-14 normwise of the double-double DFT."""
+    shape = (64, 64, 64)
+    x = S.complex_uniform(S.SEED_64, shape).numpy()
+    pl = plan(shape, mode)
+    assert splits_of(pl) == ((8, 8), (8, 8), (8, 8))
+    y = run(pl, x)
+    ref_ = oracle_full(x, splits_of(pl), -1)
+    assert bits_equal(y, ref_), mismatch_report(y, ref_)
+    err = ref.normwise_error(y, ref.dft3d_dd(x))
+    assert err < 1e-14
+
+
+@pytest.mark.parametrize("mode", OZAKI_MODES)
+def test_inverse_and_batch(mode):
+    shape = (8, 16, 24)
+    x = S.complex_gaussian(7, (3,) + shape).numpy()
+    pl = plan(shape, mode, batch=3)
+    y = run(pl, x, dir=+1)
+    ref_ = oracle_full(x, splits_of(pl), +1)
+    assert bits_equal(y, ref_), mismatch_report(y, ref_)
+
+
+@pytest.mark.parametrize("mode", OZAKI_MODES)
+def test_edge_inputs(mode):
+    shape = (8, 8, 16)
+    pl = plan(shape, mode)
+    sp = splits_of(pl)
+    cases = {
+        "zeros": np.zeros(shape, np.complex128),
+        "impulse": np.zeros(shape, np.complex128),
+        "wide": S.complex_wide_range(S.SEED_256_WIDE, shape).numpy(),
+        "subnormal": S.complex_uniform(3, shape).numpy() * 2.0 ** -1060,
+        "huge": S.complex_uniform(4, shape).numpy() * 2.0 ** 900,
+        "sparse_cols": S.complex_uniform(5, shape).numpy() * (np.arange(16) % 3 == 0),
+    }
+    cases["impulse"][0, 0, 0] = 1.0
+    for name, x in cases.items():
+        y = run(pl, x)
+        ref_ = oracle_full(x, sp, -1)
+        assert bits_equal(y, ref_), name + ": " + mismatch_report(y, ref_)
+    assert np.all(run(pl, cases["impulse"]) == 1.0)
+
+
+@pytest.mark.parametrize("mode", OZAKI_MODES)
+def test_wide_range_256_stage_sampled(mode):
+    """256^3 wide-dynamic-range input: every stage of every axis pass, run alone
+    through obfft_exec_stage, matches the oracle on sampled columns."""
+    shape = (256, 256, 256)
+    pl = plan(shape, mode)
+    x = S.complex_wide_range(S.SEED_256_WIDE, shape, device="cuda")
+    _check_pass_sampled(pl, x, shape, dir=-1, nsample=48)
+
+
+def _check_pass_sampled(pl, x, shape, dir, nsample):
+    rng = np.random.default_rng(1)
+    cur = x.contiguous()
+    scratch = torch.empty_like(cur)
+    out = torch.empty_like(cur)
+    n = list(shape)
+    for axis in (2, 1, 0):
+        p, q = pl.splits(axis)
+        N = n[axis]
+        tot = cur.numel()
+        L = tot // N
+        pl.exec_stage(axis, 1, cur, scratch, dir)
+        pl.exec_stage(axis, 2, scratch, out, dir)
+        torch.cuda.synchronize()
+        lines = rng.choice(L, size=min(nsample, L), replace=False)
+        xin = cur.reshape(L, N)[torch.from_numpy(lines).cuda()].cpu().numpy()
+        y1 = scratch.reshape(L, N)[torch.from_numpy(lines).cuda()].cpu().numpy()
+        # stage 1 on the sampled lines
+        c1 = xin.reshape(-1, q, p).transpose(0, 2, 1).reshape(-1, q)
+        r1, _, _ = ref.stage(c1, ref.table_q(q, dir), None, use_crt=False)
+        r1 = r1.reshape(-1, p, q).transpose(0, 2, 1).reshape(-1, N)  # stored [l][k2][j1]
+        assert bits_equal(y1, r1), f"axis {axis} stage 1: " + mismatch_report(y1, r1)
+        # stage 2 on the same lines (input: the GPU's stage-1 output)
+        c2 = y1.reshape(-1, q, p).reshape(-1, p)                     # columns (l, k2) over j1
+        grp = np.tile(np.arange(q, dtype=np.int32), len(lines))
+        r2, _, _ = ref.stage(c2, ref.table_p(p, q, dir), grp, use_crt=False)
+        z = r2.reshape(-1, q, p).transpose(0, 2, 1).reshape(-1, N)   # Y[k2 + q k1]
+        # the output is rotated: [B][N][P] with P = L (batch 1)
+        got = out.reshape(N, L)[:, torch.from_numpy(lines).cuda()].T.cpu().numpy()
+        assert bits_equal(got, z), f"axis {axis} stage 2: " + mismatch_report(got, z)
+        cur, out = out, cur  # the rotated output is the next pass's input
+
+
+def test_fp64_native_accuracy_and_ozaki_within_2x():
+    shape = (32, 32, 32)
+    x = S.complex_uniform(S.SEED_64, shape).numpy()
+    yd = ref.dft3d_dd(x)
+    e64 = ref.normwise_error(run(plan(shape, "fp64"), x), yd)
+    assert e64 < 1e-14
+    for mode in OZAKI_MODES:
+        e = ref.normwise_error(run(plan(shape, mode), x), yd)
+        assert e < 1e-14 and e <= 2 * e64 + 1e-16, (mode, e, e64)
+
+
+def test_fp64_native_mixed_radix():
+    shape = (12, 96, 10)
+    x = S.complex_gaussian(9, shape).numpy()
+    y = run(plan(shape, "fp64"), x)
+    assert ref.normwise_error(y, ref.dft3d_dd(x)) < 1e-14
+
+
+def test_roundtrip_all_modes():
+    shape = (16, 32, 64)
+    x = S.complex_wide_range(S.SEED_256_WIDE, shape).numpy()
+    N = np.prod(shape)
+    for mode in OZAKI_MODES + ["fp64"]:
+        pl = plan(shape, mode)
+        y = run(pl, x, -1)
+        back = run(pl, y, +1) / N
+        assert np.linalg.norm(back - x) / np.linalg.norm(x) < 1e-14, mode
+
+
+def test_error_paths_on_device():
+    from paper_2606_23698_gb300 import ObfftError
+    pl = plan((8, 8, 8), "int8")
+    x = torch.zeros(512, dtype=torch.complex128, device="cuda")
+    with pytest.raises(ObfftError):
+        from paper_2606_23698_gb300 import _lib
+        _lib.obfft_exec(pl.handle, x.data_ptr(), x.data_ptr(), -1, 0)      # in == out
+    with pytest.raises(ObfftError):
+        _lib.obfft_exec(pl.handle, x.data_ptr() + 8, x.data_ptr(), -1, 0)  # misaligned
+    with pytest.raises(ObfftError):
+        _lib.obfft_exec(pl.handle, x.data_ptr(), x.data_ptr(), 0, 0)       # bad dir
