@@ -33,6 +33,13 @@ struct ModConsts {
     uint32_t halfM32[4];      // M / 2 (M is even)
     uint8_t us[NMOD][S_RAW];  // byte slices of u_k (Phase A B-matrix)
     uint8_t ws[NMOD][S_FRAC]; // byte slices of w_k = round(2^48 u_k / M)
+    // FP8-mode epilogue constants (exact small integers as floats)
+    float fm[NMOD];    // m
+    float finv[NMOD];  // 1/m rounded
+    float fhalf[NMOD]; // m/2
+    float fsq[NMOD];   // s for m = s^2, else 0
+    float fc3[NMOD];   // 16^3 mod m
+    float fc4[NMOD];   // 16^4 mod m
 };
 
 // Host-side constant generation (plan.cpp).
@@ -52,6 +59,8 @@ struct AxisTables {
     // INT8 mode: fragment-native s8 limb tables, stage 1 (1 group) / stage 2 (q groups)
     void *int8_s1 = nullptr, *int8_s2 = nullptr;
     size_t int8_s1_bytes = 0, int8_s2_bytes = 0;
+    // FP8 mode: E4M3 digit planes of the constant matrices, stage 1 / stage 2
+    void *fp8_s1 = nullptr, *fp8_s2 = nullptr;
     // FP64 native comparator: twiddles exp(dir 2 pi i m / n) for m < n as double pairs
     double *tw = nullptr;
     // quantised int64 constants (kept for the FP8 path and for debugging)
@@ -74,6 +83,8 @@ struct obfft_plan_s {
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     obfft::ModConsts *d_consts = nullptr;
+    void *d_pab = nullptr;     // Phase A B-matrix (FP16 u_k / w_k byte slices)
+    int *d_status = nullptr;   // device status word (bounded-wait timeouts)
 };
 
 namespace obfft {
@@ -90,6 +101,11 @@ struct StageGeom {
 };
 cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const StageGeom &g,
                               int stage, const double2 *in, double2 *out, cudaStream_t s);
+cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
+                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
+size_t fp8_smem_bytes(int Kout, int npad);
+std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K);
+std::vector<uint8_t> build_phase_a_b();
 cudaError_t launch_stage_fp64(const AxisTables &t, const StageGeom &g, int stage,
                               const double2 *in, double2 *out, cudaStream_t s);
 }  // namespace obfft

@@ -73,6 +73,15 @@ void make_mod_consts(ModConsts *mc) {
         u128 wk = (((u128)y << 49) + m) / ((u128)2 * m);
         for (int t = 0; t < S_FRAC; t++) mc->ws[k][t] = (uint8_t)(wk >> (8 * t));
         mc->yk_over_mk[k] = (float)((double)y / (double)m);
+        mc->fm[k] = (float)m;
+        mc->finv[k] = (float)(1.0 / (double)m);
+        mc->fhalf[k] = (float)m * 0.5f;
+        int sq = 0;
+        for (int t = 1; t * t <= (int)m; t++)
+            if (t * t == (int)m) sq = t;
+        mc->fsq[k] = (float)sq;
+        mc->fc3[k] = (float)(4096 % m);
+        mc->fc4[k] = (float)(65536 % m);
     }
     for (int w = 0; w < 4; w++) {
         mc->M32[w] = (uint32_t)(M >> (32 * w));
@@ -230,6 +239,107 @@ static std::vector<uint32_t> build_int8_table(const std::vector<int64_t> &F, int
     return out;
 }
 
+// ------------------------------------------------------------ FP8 tables
+static uint8_t e4m3_of_int(int v) {  // exact for |v| <= 16
+    if (v == 0) return 0;
+    uint8_t sgn = v < 0 ? 0x80 : 0;
+    int a = v < 0 ? -v : v;
+    int e = 31 - __builtin_clz((unsigned)a);
+    int mant = ((a << 3) >> e) & 7;
+    return (uint8_t)(sgn | ((e + 7) << 3) | mant);
+}
+static uint16_t f16_of_small(int v) {  // exact for 0 <= v < 2048
+    if (v == 0) return 0;
+    int e = 31 - __builtin_clz((unsigned)v);
+    int mant = ((v << 10) >> e) & 0x3FF;
+    return (uint16_t)(((e + 15) << 10) | mant);
+}
+static int64_t rne_div(int64_t v, int64_t d) {  // round-half-even of v / d, d > 0
+    int64_t q = v >= 0 ? v / d : -((-v) / d);
+    int64_t r = v - q * d;
+    if (2 * r > d || (2 * r == d && (q & 1))) q += 1;
+    if (2 * r < -d || (2 * r == -d && (q & 1))) q -= 1;
+    return q;
+}
+// balanced digits of a residue for modulus index k (same decomposition rules
+// as the device: m = s^2 -> (h, l); 9-bit -> (d0, d1); 11-bit -> (d0, d1, d2))
+static int fp8_digits(int k, int64_t v, int dig[3]) {
+    const int64_t m = kModuli[k];
+    if (k >= 3 && k < 9) {
+        int64_t s = 0;
+        while ((s + 1) * (s + 1) <= m) s++;
+        int64_t h = rne_div(v, s);
+        dig[0] = (int)h;
+        dig[1] = (int)(v - s * h);
+        return 2;
+    }
+    if (k >= 9) {
+        int64_t d1 = rne_div(v, 16);
+        dig[0] = (int)(v - 16 * d1);
+        dig[1] = (int)d1;
+        return 2;
+    }
+    int64_t d2 = rne_div(v, 256), r = v - 256 * d2, d1 = rne_div(r, 16);
+    dig[0] = (int)(r - 16 * d1);
+    dig[1] = (int)d1;
+    dig[2] = (int)d2;
+    return 3;
+}
+
+std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K) {
+    const int npad = K <= 16 ? 16 : 32;
+    const size_t planeB = (size_t)npad * 32;
+    std::vector<uint8_t> out((size_t)groups * 81 * planeB, 0);
+    size_t off = 0;
+    for (int g = 0; g < groups; g++)
+        for (int k = 0; k < NMOD; k++) {
+            const int64_t m = kModuli[k];
+            const int nd = k < 3 ? 3 : 2;
+            for (int p = 0; p < 3; p++) {
+                for (int n = 0; n < K; n++)
+                    for (int j = 0; j < K; j++) {
+                        const int64_t *e = &F[(((size_t)g * K + n) * K + j) * 2];
+                        int64_t a = p == 0 ? e[0] : p == 1 ? e[1] : e[0] + e[1];
+                        int64_t r = modc(a, m);
+                        int64_t v = 2 * r > m ? r - m : r;  // balanced
+                        int dig[3];
+                        fp8_digits(k, v, dig);
+                        for (int d = 0; d < nd; d++) {
+                            size_t pos = off + (size_t)(p * nd + d) * planeB + (size_t)(n / 8) * 256 +
+                                         (size_t)(j / 16) * 128 + (n % 8) * 16 + j % 16;
+                            out[pos] = e4m3_of_int(dig[d]);
+                        }
+                    }
+            }
+            off += (size_t)3 * nd * planeB;
+        }
+    return out;
+}
+
+// Phase A B-matrix: 48 rows (Re: 15 u-slices, 6 w-slices, 3 zero; Im: same)
+// x 32 K (Re residues 0..11, Im residues 12..23, 8 zero), FP16, K-major
+// canonical layout (LBO 128, SBO 512).
+std::vector<uint8_t> build_phase_a_b() {
+    ModConsts mc;
+    make_mod_consts(&mc);
+    std::vector<uint8_t> out(48 * 64, 0);
+    for (int n = 0; n < 48; n++) {
+        int part = n / 24, col = n % 24;
+        for (int kk = 0; kk < 32; kk++) {
+            int val = 0;
+            if (kk < 24 && kk / 12 == part && col < 21) {
+                int k = kk % 12;
+                val = col < S_RAW ? mc.us[k][col] : mc.ws[k][col - S_RAW];
+            }
+            uint16_t h = f16_of_small(val);
+            size_t pos = (size_t)(n / 8) * 512 + (size_t)(kk / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2;
+            out[pos] = (uint8_t)(h & 0xFF);
+            out[pos + 1] = (uint8_t)(h >> 8);
+        }
+    }
+    return out;
+}
+
 static void fill_matrices(AxisTables &t) {
     const int p = t.p, q = t.q, n = t.n, dir = t.dir;
     t.Fq.assign((size_t)q * q * 2, 0);
@@ -263,6 +373,11 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
         t.int8_s2_bytes = s2.size() * 4;
         e = upload(s1.data(), t.int8_s1_bytes, &t.int8_s1);
         if (e == cudaSuccess) e = upload(s2.data(), t.int8_s2_bytes, &t.int8_s2);
+    } else if (P->mode == OBFFT_MODE_FP8) {
+        std::vector<uint8_t> s1 = build_fp8_planes(t.Fq, 1, t.q);
+        std::vector<uint8_t> s2 = build_fp8_planes(t.Fp, t.q, t.p);
+        e = upload(s1.data(), s1.size(), &t.fp8_s1);
+        if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
     } else if (P->mode == OBFFT_MODE_FP64_NATIVE) {
         std::vector<double> tw;
         auto push = [&](int N) {
@@ -291,7 +406,7 @@ AxisTables *get_tables(obfft_plan P, int n, int pp, int qq, int dir) {
 }
 
 // Bailey split: q = smallest divisor >= sqrt(n), p = n / q; both <= 64.
-static bool choose_split(int64_t n, AxisPlan *a) {
+static bool choose_split(int64_t n, AxisPlan *a, int kmax = KMAX) {
     if (n == 1) {
         a->n = 1; a->p = 1; a->q = 1;
         return true;
@@ -299,7 +414,7 @@ static bool choose_split(int64_t n, AxisPlan *a) {
     for (int64_t q = 1; q <= n; q++)
         if (n % q == 0 && q * q >= n) {
             int64_t p = n / q;
-            if (p > KMAX || q > KMAX) return false;
+            if (p > kmax || q > kmax) return false;
             a->n = (int)n; a->p = (int)p; a->q = (int)q;
             return true;
         }
@@ -310,6 +425,8 @@ static void free_tables(obfft_plan P) {
     for (auto &t : P->tables) {
         cudaFree(t.int8_s1);
         cudaFree(t.int8_s2);
+        cudaFree(t.fp8_s1);
+        cudaFree(t.fp8_s2);
         cudaFree(t.tw);
     }
     P->tables.clear();
@@ -362,7 +479,17 @@ static obfft_status new_plan(int mode, obfft_plan *P) {
     ModConsts mc;
     make_mod_consts(&mc);
     cudaError_t e = upload(&mc, sizeof(mc), (void **)&p->d_consts);
+    if (e == cudaSuccess) {
+        std::vector<uint8_t> pab = build_phase_a_b();
+        e = upload(pab.data(), pab.size(), &p->d_pab);
+    }
+    if (e == cudaSuccess) {
+        int zero = 0;
+        e = upload(&zero, sizeof(int), (void **)&p->d_status);
+    }
     if (e != cudaSuccess) {
+        cudaFree(p->d_consts);
+        cudaFree(p->d_pab);
         delete p;
         return set_error(OBFFT_ERR_ALLOC, std::string("constants: ") + cudaGetErrorString(e));
     }
@@ -377,11 +504,12 @@ extern "C" obfft_status obfft_plan_create(obfft_plan *out, int64_t n0, int64_t n
     if (n0 < 1 || n1 < 1 || n2 < 1 || batch < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
     GridDesc gd;
     gd.n[0] = n0; gd.n[1] = n1; gd.n[2] = n2;
+    const int kmax = mode == OBFFT_MODE_FP8 ? 32 : KMAX;
     for (int a = 0; a < 3; a++)
-        if (!choose_split(gd.n[a], &gd.ax[a]))
+        if (!choose_split(gd.n[a], &gd.ax[a], kmax))
             return set_error(OBFFT_ERR_UNSUPPORTED_SIZE,
                              "axis " + std::to_string(a) + " of length " + std::to_string(gd.n[a]) +
-                                 " does not factor as p*q with p, q <= 64");
+                                 " does not factor as p*q with p, q <= " + std::to_string(kmax));
     obfft_plan P;
     obfft_status st = new_plan(mode, &P);
     if (st != OBFFT_OK) return st;
@@ -400,9 +528,9 @@ extern "C" obfft_status obfft_plan_create_many(obfft_plan *out, int count, const
         for (int a = 0; a < 3; a++) {
             gd.n[a] = dims[g * 3 + a];
             if (gd.n[a] < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
-            if (!choose_split(gd.n[a], &gd.ax[a]))
+            if (!choose_split(gd.n[a], &gd.ax[a], mode == OBFFT_MODE_FP8 ? 32 : KMAX))
                 return set_error(OBFFT_ERR_UNSUPPORTED_SIZE, "axis length " + std::to_string(gd.n[a]) +
-                                                                 " does not factor as p*q with p, q <= 64");
+                                                                 " does not factor within the mode's p, q limit");
         }
         grids.push_back(gd);
     }
@@ -421,6 +549,8 @@ extern "C" obfft_status obfft_destroy(obfft_plan p) {
     free_tables(p);
     cudaFree(p->scratch);
     cudaFree(p->d_consts);
+    cudaFree(p->d_pab);
+    cudaFree(p->d_status);
     cudaSetDevice(cur);
     delete p;
     return OBFFT_OK;
@@ -454,6 +584,8 @@ static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, i
     cudaError_t e;
     if (P->mode == OBFFT_MODE_INT8)
         e = launch_stage_int8(*t, P->d_consts, g, stage, in, out, s);
+    else if (P->mode == OBFFT_MODE_FP8)
+        e = launch_stage_fp8(*t, P->d_consts, P->d_pab, P->d_status, g, stage, in, out, s);
     else if (P->mode == OBFFT_MODE_FP64_NATIVE)
         e = launch_stage_fp64(*t, g, stage, in, out, s);
     else

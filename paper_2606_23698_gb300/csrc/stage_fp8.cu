@@ -1,0 +1,503 @@
+// FP8-mode Bailey stage on Blackwell tensor cores (tcgen05, sm_103a).
+//
+// One CTA transforms 128 columns (one Ozaki-II complex GEMM per column,
+// Algorithm 1, one half).  Per modulus m_k and Karatsuba product
+// (D = A_R B_R, E = A_I B_I, F = (A_R + A_I)(B_R + B_I), Background):
+//   * the data residues (canonical x~ mod m_k, then balanced) are split into
+//     E4M3-exact digit planes by the SIMT threads and stored to shared memory
+//     in the UMMA K-major layout (row = column of the DFT, 32 bytes of K);
+//   * the constant DFT / twiddle-fused matrix digits arrive by TMA bulk copy;
+//   * tcgen05.mma kind::f8f6f4 (M = 128, N = 16/32, K = 32) accumulates each
+//     weight class of digit products in TMEM (FP32, every partial sum an
+//     integer far below 2^24: exact);
+//   * the epilogue reads the classes back (tcgen05.ld), recombines them with
+//     their weights, reduces mod m_k, forms R_k = D - E and I_k = F - D - E,
+//     canonicalises to [0, m_k) and writes the FP16 CRT operand
+//     (Sec. tcgarner: residues < 2048 are FP16-exact) to shared memory.
+// After the 12 moduli, CRT Phase A runs as tcgen05.mma kind::f16 (M = 128
+// complex outputs, N = 48 = Re/Im x (15 byte slices of u_k + 6 of w_k + 3
+// pad), K = 24 = Re/Im x 12 moduli, FP32 accumulation exact below 2^24,
+// Eq. phaseAcost), and each thread finishes its outputs with the Kulisch
+// sum E = sum_s P_s 256^s, the lift quotient from the w_k columns, the
+// two-sided modulo-M correction and the correctly rounded pack (Algorithm 2).
+//
+// Digit layouts (exhaustively verified on the host, see the FP8 layout tests):
+//   m = s^2 (1089, 1024, 961, 841, 625, 529): v = s h + l, |h|, |l| <= 16;
+//       a b = s (a_h b_l + a_l b_h) + a_l b_l (mod m): classes {s: 2 products, 1: 1}.
+//   511, 491, 487: v = d0 + 16 d1, |d0| <= 8, |d1| <= 16: classes 16^w, w = 0..2.
+//   2039, 2029, 2027: v = d0 + 16 d1 + 256 d2, |d0|,|d1| <= 8, |d2| <= 4:
+//       classes 16^w (w = 0..4), 16^3 and 16^4 reduced mod m.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "obfft_internal.h"
+#include "tc_common.cuh"
+
+namespace obfft {
+
+// modulus kinds, in the order of kModuli
+enum : int { KIND_B11 = 0, KIND_SQ = 1, KIND_B9 = 2 };
+__host__ __device__ constexpr int fp8_kind(int k) { return k < 3 ? KIND_B11 : (k < 9 ? KIND_SQ : KIND_B9); }
+__host__ __device__ constexpr int fp8_ndig(int k) { return fp8_kind(k) == KIND_B11 ? 3 : 2; }
+__host__ __device__ constexpr int fp8_ncls(int k) {
+    return fp8_kind(k) == KIND_B11 ? 5 : (fp8_kind(k) == KIND_SQ ? 2 : 3);
+}
+// planes before modulus k in a per-group table: sum_{k' < k} 3 * ndig(k')
+__host__ __device__ constexpr int fp8_plane_offset(int k) {
+    int s = 0;
+    for (int i = 0; i < k; i++) s += 3 * fp8_ndig(i);
+    return s;
+}
+constexpr int FP8_PLANES_PER_GROUP = 81;  // 3 * (3*3 + 6*2 + 3*2)
+
+constexpr int FP8_THREADS = 256;
+constexpr int PA_N = 48;          // Phase A output columns (Re 24 | Im 24)
+constexpr int PA_ROWB = 384;      // bytes per 8-row group of the staging (3 K-chunks)
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+struct ColMapT {
+    int stage;
+    int64_t L, Lpad, P;
+    int n, p, q;
+    __device__ __forceinline__ bool valid(int64_t c, int64_t ncols) const {
+        if (c >= ncols) return false;
+        if (stage == 2) return (c % Lpad) < L;
+        return true;
+    }
+    __device__ __forceinline__ int64_t in_index(int64_t c, int j) const {
+        if (stage == 1) {
+            int64_t l = c / p, j1 = c % p;
+            return l * n + j1 + (int64_t)p * j;
+        }
+        int64_t k2 = c / Lpad, l = c % Lpad;
+        return l * n + k2 * p + j;
+    }
+    __device__ __forceinline__ int64_t out_index(int64_t c, int k) const {
+        if (stage == 1) {
+            int64_t l = c / p, j1 = c % p;
+            return l * n + (int64_t)k * p + j1;
+        }
+        int64_t k2 = c / Lpad, l = c % Lpad;
+        int64_t b = l / P, r = l % P;
+        return (b * n + k2 + (int64_t)q * k) * P + r;
+    }
+    __device__ __forceinline__ int group(int64_t c) const { return stage == 1 ? 0 : (int)(c / Lpad); }
+};
+
+// byte offset of element (row, k) of the Phase-A staging (K-major, 3 chunks of 8 f16)
+__device__ __forceinline__ uint32_t stage_off(uint32_t row, uint32_t k) {
+    return (row >> 3) * PA_ROWB + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// E4M3 digit planes of balanced residues for one modulus: writes this thread's
+// 16 bytes (elements 16*hf .. 16*hf+15 of row c) of each digit plane.
+template <int KIND>
+__device__ __forceinline__ void write_digits(const float (&v)[16], uint8_t *sA, int c, int hf, float s) {
+    constexpr int ND = KIND == KIND_B11 ? 3 : 2;
+    uint32_t words[ND][4];
+#pragma unroll
+    for (int q4 = 0; q4 < 4; q4++) {
+        uint32_t pk[ND][2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; h2++) {
+            float dg[ND][2];
+#pragma unroll
+            for (int e2 = 0; e2 < 2; e2++) {
+                float x = v[q4 * 4 + h2 * 2 + e2];
+                if constexpr (KIND == KIND_SQ) {
+                    float h = rint_small(x * (1.0f / s));  // s h + l
+                    dg[0][e2] = h;
+                    dg[1][e2] = __fmaf_rn(-s, h, x);
+                } else if constexpr (KIND == KIND_B9) {
+                    float d1 = rint_small(x * 0.0625f);
+                    dg[1][e2] = d1;
+                    dg[0][e2] = __fmaf_rn(-16.0f, d1, x);
+                } else {
+                    float d2 = rint_small(x * 0.00390625f);
+                    float r = __fmaf_rn(-256.0f, d2, x);
+                    float d1 = rint_small(r * 0.0625f);
+                    dg[ND - 1][e2] = d2;
+                    dg[1][e2] = d1;
+                    dg[0][e2] = __fmaf_rn(-16.0f, d1, r);
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < ND; d++) pk[d][h2] = e4m3x2(dg[d][0], dg[d][1]);
+        }
+#pragma unroll
+        for (int d = 0; d < ND; d++) words[d][q4] = pk[d][0] | (pk[d][1] << 16);
+    }
+    const uint32_t rowoff = (uint32_t)(c >> 3) * 256 + (uint32_t)hf * 128 + (uint32_t)(c & 7) * 16;
+#pragma unroll
+    for (int d = 0; d < ND; d++)
+        *reinterpret_cast<uint4 *>(sA + d * 4096 + rowoff) =
+            make_uint4(words[d][0], words[d][1], words[d][2], words[d][3]);
+}
+
+// Issue the digit-pair MMAs of one (modulus, product) into class accumulators.
+template <int KIND>
+__device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t sA, uint32_t sBp, int npad,
+                                               uint32_t idesc) {
+    const uint32_t planeB = (uint32_t)npad * 32;
+    auto mma = [&](int ci, int dj, int cls, uint32_t acc) {
+        uint64_t a = smem_desc(sA + dj * 4096, 128, 256);
+        uint64_t b = smem_desc(sBp + ci * planeB, 128, 256);
+        tc_mma_f8(tmem + cls * npad, a, b, idesc, acc);
+    };
+    if (KIND == KIND_SQ) {        // digits 0 = h, 1 = l
+        mma(0, 1, 1, 0);          // a_h b_l
+        mma(1, 0, 1, 1);          // a_l b_h
+        mma(1, 1, 0, 0);          // a_l b_l
+    } else if (KIND == KIND_B9) {
+        mma(0, 0, 0, 0);
+        mma(0, 1, 1, 0);
+        mma(1, 0, 1, 1);
+        mma(1, 1, 2, 0);
+    } else {
+        mma(0, 0, 0, 0);
+        mma(0, 1, 1, 0);
+        mma(1, 0, 1, 1);
+        mma(0, 2, 2, 0);
+        mma(1, 1, 2, 1);
+        mma(2, 0, 2, 1);
+        mma(1, 2, 3, 0);
+        mma(2, 1, 3, 1);
+        mma(2, 2, 4, 0);
+    }
+}
+
+// Read this thread's NH class accumulators (lane = row, columns hf*NH ..) and
+// recombine: returns the balanced residue of sum_j a_j b_j mod m.
+template <int KIND, int NH>
+__device__ __forceinline__ void read_product(uint32_t tlane, int npad, int hf, const ModConsts &mc, int k,
+                                             float (&out)[NH]) {
+    constexpr int NC = KIND == KIND_B11 ? 5 : (KIND == KIND_SQ ? 2 : 3);
+    float acc[NH];
+#pragma unroll
+    for (int i = 0; i < NH; i++) acc[i] = 0.f;
+    float wts[5];
+    if (KIND == KIND_SQ) {
+        wts[0] = 1.f;
+        wts[1] = mc.fsq[k];
+    } else {
+        wts[0] = 1.f;
+        wts[1] = 16.f;
+        wts[2] = 256.f;
+        wts[3] = mc.fc3[k];
+        wts[4] = mc.fc4[k];
+    }
+#pragma unroll
+    for (int cl = 0; cl < NC; cl++) {
+        uint32_t taddr = tlane + (uint32_t)(cl * npad + hf * NH);
+        if (NH == 16) {
+            uint32_t r[16];
+            tmem_ld16(taddr, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; i++) acc[i] = __fmaf_rn(wts[cl], __uint_as_float(r[i]), acc[i]);
+        } else {
+            uint32_t r[8];
+            tmem_ld8(taddr, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; i++) acc[i] = __fmaf_rn(wts[cl], __uint_as_float(r[i]), acc[i]);
+        }
+    }
+    const float m = mc.fm[k], im = mc.finv[k];
+#pragma unroll
+    for (int i = 0; i < NH; i++) out[i] = __fmaf_rn(-m, rint_small(acc[i] * im), acc[i]);
+}
+
+// canonical residue in [0, m) of an exact small integer x (|x| < 2^20), FP32
+__device__ __forceinline__ float canon(float x, float m, float im) {
+    float r = __fmaf_rn(-m, floorf(x * im), x);
+    r = r < 0.f ? r + m : r;
+    return r >= m ? r - m : r;
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(FP8_THREADS, 1)
+    stage_fp8_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab,
+                     const ModConsts *__restrict__ gmc, ColMapT map, int64_t ncols, int K, int Kout,
+                     const double2 *__restrict__ in, double2 *__restrict__ out, int *status) {
+    constexpr int NH = NPAD / 2;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ ModConsts mc;
+    __shared__ int colpart[2][128];
+    __shared__ __align__(8) uint64_t mbar[3];  // 0: B planes (TMA), 1: MMA, 2: Phase-A B (TMA)
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int c = 32 * (w & 3) + lane, hf = w >> 2;
+    const uint32_t lanebase = (uint32_t)(32 * (w & 3)) << 16;
+    const int64_t cbase = (int64_t)blockIdx.x * 128;
+    const int64_t cg = cbase + c;
+    const bool cvalid = map.valid(cg, ncols);
+    const int group = map.group(cbase);
+
+    const uint32_t stage_rows = (uint32_t)Kout * 128;
+    const uint32_t stage_bytes = (stage_rows >> 3) * PA_ROWB + 128;
+    uint8_t *sStage = smem;
+    uint8_t *sA = smem + ((stage_bytes + 1023) & ~1023u);
+    uint8_t *sB = sA + 3 * 4096;
+    uint8_t *sPAB = sB + 9 * NPAD * 32;
+    const uint32_t planeB = NPAD * 32;
+    const uint8_t *gplanes = planes + (size_t)group * FP8_PLANES_PER_GROUP * planeB;
+
+    for (int i = tid; i < (int)(sizeof(ModConsts) / 4); i += FP8_THREADS)
+        reinterpret_cast<uint32_t *>(&mc)[i] = reinterpret_cast<const uint32_t *>(gmc)[i];
+    // zero the staging tail (aliased K-chunk of the last row group)
+    if (tid < 32) reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[tid] = 0u;
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        mbar_init(smem_u32(&mbar[2]), 1);
+        mbar_fence_init();
+    }
+    if (w == 0) tmem_alloc(smem_u32(&tmem_holder), 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+    if (tid == 0) {
+        mbar_expect_tx(smem_u32(&mbar[2]), PA_N * 64);
+        tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[2]));
+        uint32_t bytes0 = 3 * fp8_ndig(0) * planeB;
+        mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
+        tma_bulk_g2s(smem_u32(sB), gplanes, bytes0, smem_u32(&mbar[0]));
+    }
+
+    // ---------------- deconstruction: x~ of this thread's 16 elements ----------------
+    uint64_t xb[16][2];
+    int lead = LEAD_ZERO;
+#pragma unroll
+    for (int jj = 0; jj < 16; jj++) {
+        int j = 16 * hf + jj;
+        double2 x = make_double2(0.0, 0.0);
+        if (cvalid && j < K) x = in[map.in_index(cg, j)];
+        xb[jj][0] = (uint64_t)__double_as_longlong(x.x);
+        xb[jj][1] = (uint64_t)__double_as_longlong(x.y);
+        lead = max(lead, max(lead_exponent(xb[jj][0]), lead_exponent(xb[jj][1])));
+    }
+    colpart[hf][c] = lead;
+    __syncthreads();
+    int lead2 = max(colpart[0][c], colpart[1][c]);
+    const int e = lead2 == LEAD_ZERO ? 0 : lead2;
+    Pieces pR[16], pI[16];
+#pragma unroll
+    for (int jj = 0; jj < 16; jj++) {
+        pR[jj] = split_pieces(scale_round(xb[jj][0], e));
+        pI[jj] = split_pieces(scale_round(xb[jj][1], e));
+    }
+
+    uint32_t mma_phase = 0;
+    bool ok = true;
+    float Dp[NH], Ep[NH];
+    // ---------------- per modulus: digit planes, FP8 MMAs, residue epilogue ----------
+    for (int k = 0; k < NMOD && ok; k++) {
+        ok = mbar_wait(smem_u32(&mbar[0]), (uint32_t)(k & 1), WAIT_LIMIT);
+        const int kind = fp8_kind(k);
+        const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
+        const float mf = mc.fm[k], halfm = mc.fhalf[k], imf = mc.finv[k];
+        uint32_t rR[16], rI[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; jj++) {
+            rR[jj] = residue(pR[jj], m, mu, c20, c40, cn);
+            rI[jj] = residue(pI[jj], m, mu, c20, c40, cn);
+        }
+        for (int p = 0; p < 3; p++) {
+            float v[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                uint32_t r = p == 0 ? rR[jj] : (p == 1 ? rI[jj] : rR[jj] + rI[jj]);
+                r = r >= m ? r - m : r;
+                float f = __uint_as_float(0x4B000000u | r) - 8388608.0f;  // exact r
+                v[jj] = f > halfm ? f - mf : f;                            // balanced
+            }
+            if (kind == KIND_SQ)
+                write_digits<KIND_SQ>(v, sA, c, hf, mc.fsq[k]);
+            else if (kind == KIND_B9)
+                write_digits<KIND_B9>(v, sA, c, hf, 0.f);
+            else
+                write_digits<KIND_B11>(v, sA, c, hf, 0.f);
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t idesc = instr_desc(128, NPAD, 0);
+                const uint32_t sBp = smem_u32(sB) + (uint32_t)(p * fp8_ndig(k)) * planeB;
+                if (kind == KIND_SQ)
+                    issue_products<KIND_SQ>(tmem, smem_u32(sA), sBp, NPAD, idesc);
+                else if (kind == KIND_B9)
+                    issue_products<KIND_B9>(tmem, smem_u32(sA), sBp, NPAD, idesc);
+                else
+                    issue_products<KIND_B11>(tmem, smem_u32(sA), sBp, NPAD, idesc);
+                tc_commit(smem_u32(&mbar[1]));
+            }
+            bool okm = mbar_wait(smem_u32(&mbar[1]), mma_phase, WAIT_LIMIT);
+            mma_phase ^= 1;
+            tc_fence_after();
+            float res[NH];
+            if (okm) {
+                if (kind == KIND_SQ)
+                    read_product<KIND_SQ, NH>(tmem + lanebase, NPAD, hf, mc, k, res);
+                else if (kind == KIND_B9)
+                    read_product<KIND_B9, NH>(tmem + lanebase, NPAD, hf, mc, k, res);
+                else
+                    read_product<KIND_B11, NH>(tmem + lanebase, NPAD, hf, mc, k, res);
+            } else {
+                atomicExch(&abort_flag, 1);
+            }
+            if (p == 0) {
+#pragma unroll
+                for (int i = 0; i < NH; i++) Dp[i] = okm ? res[i] : 0.f;
+            } else if (p == 1) {
+#pragma unroll
+                for (int i = 0; i < NH; i++) Ep[i] = okm ? res[i] : 0.f;
+            } else if (okm) {
+                // Karatsuba combine in the residue domain, canonicalise, FP16 -> staging
+#pragma unroll
+                for (int i = 0; i < NH; i++) {
+                    int kout = hf * NH + i;
+                    if (kout >= Kout) continue;
+                    float Rv = canon(Dp[i] - Ep[i], mf, imf);
+                    float Iv = canon(res[i] - Dp[i] - Ep[i], mf, imf);
+                    uint32_t row = (uint32_t)kout * 128 + c;
+                    uint32_t hv = f16x2(Rv, Iv);  // exact: canonical residues < 2048
+                    *reinterpret_cast<uint16_t *>(sStage + stage_off(row, k)) = (uint16_t)(hv & 0xFFFFu);
+                    *reinterpret_cast<uint16_t *>(sStage + stage_off(row, 12 + k)) = (uint16_t)(hv >> 16);
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (abort_flag) ok = false;
+        }
+        if (ok && tid == 0 && k + 1 < NMOD) {
+            uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
+            mbar_expect_tx(smem_u32(&mbar[0]), bytes);
+            tma_bulk_g2s(smem_u32(sB), gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes,
+                         smem_u32(&mbar[0]));
+        }
+    }
+
+    // ---------------- CRT Phase A on FP16 tensor cores, then Kulisch + lift + pack ----
+    if (ok) {
+        fence_async_smem();
+        __syncthreads();
+        ok = mbar_wait(smem_u32(&mbar[2]), 0, WAIT_LIMIT);
+        const uint32_t idescA = instr_desc(128, PA_N, 0);
+        const int per_wave = 10;
+        for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
+            const int nb = min(per_wave, Kout - b0);
+            if (tid == 0) {
+                tc_fence_after();
+                for (int bi = 0; bi < nb; bi++) {
+                    uint32_t aaddr = smem_u32(sStage) + (uint32_t)(b0 + bi) * 16 * PA_ROWB;
+                    uint32_t d = tmem + (uint32_t)(bi * PA_N);
+                    tc_mma_f16(d, smem_desc(aaddr, 128, PA_ROWB), smem_desc(smem_u32(sPAB), 128, 512), idescA, 0);
+                    tc_mma_f16(d, smem_desc(aaddr + 256, 128, PA_ROWB), smem_desc(smem_u32(sPAB) + 256, 128, 512),
+                               idescA, 1);
+                }
+                tc_commit(smem_u32(&mbar[1]));
+            }
+            bool okm = mbar_wait(smem_u32(&mbar[1]), mma_phase, WAIT_LIMIT);
+            mma_phase ^= 1;
+            tc_fence_after();
+            if (okm) {
+                for (int bi = hf; bi < nb; bi += 2) {
+                    const int kout = b0 + bi;
+                    uint32_t r0[16], r1[16], r2[16];
+                    uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
+                    tmem_ld16(ta, r0);
+                    tmem_ld16(ta + 16, r1);
+                    tmem_ld16(ta + 32, r2);
+                    tmem_wait_ld();
+                    uint32_t words[48];
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        words[i] = r0[i];
+                        words[16 + i] = r1[i];
+                        words[32 + i] = r2[i];
+                    }
+                    double res[2];
+#pragma unroll
+                    for (int part = 0; part < 2; part++) {
+                        const uint32_t *wv = words + 24 * part;
+                        uint64_t acc[4] = {0, 0, 0, 0};
+#pragma unroll
+                        for (int s = 0; s < S_RAW; s++) {
+                            uint32_t P = __float_as_uint(__uint_as_float(wv[s]) + 8388608.0f) & 0x7FFFFFu;
+                            acc[s >> 2] += (uint64_t)P << (8 * (s & 3));
+                        }
+                        u128 E = (u128)acc[0] + ((u128)acc[1] << 32) + ((u128)acc[2] << 64) + ((u128)acc[3] << 96);
+                        uint64_t zacc = 0;
+#pragma unroll
+                        for (int t = 0; t < S_FRAC; t++) {
+                            uint32_t Q = __float_as_uint(__uint_as_float(wv[15 + t]) + 8388608.0f) & 0x7FFFFFu;
+                            zacc += (uint64_t)Q << (8 * t);
+                        }
+                        int64_t zhat = (int64_t)((zacc + (1ull << 47)) >> 48);
+                        i128 R = lift_two_sided(E, zhat, mc);
+                        res[part] = pack_rne(R, e - 104);
+                    }
+                    if (cvalid && kout < Kout) out[map.out_index(cg, kout)] = make_double2(res[0], res[1]);
+                }
+            } else {
+                atomicExch(&abort_flag, 1);
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (abort_flag) ok = false;
+        }
+    }
+    if (!ok && tid == 0) {
+        atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
+        // give in-flight tensor-core work a bounded chance to drain before freeing TMEM
+        mbar_wait(smem_u32(&mbar[1]), mma_phase, WAIT_LIMIT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tmem, 512);
+}
+
+size_t fp8_smem_bytes(int Kout, int npad) {
+    size_t stage_bytes = (size_t)Kout * 128 / 8 * PA_ROWB + 128;
+    return ((stage_bytes + 1023) & ~(size_t)1023) + 3 * 4096 + 9 * (size_t)npad * 32 + PA_N * 64;
+}
+
+cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
+                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s) {
+    ColMapT map;
+    map.stage = stage;
+    map.L = g.L;
+    map.Lpad = (g.L + 127) / 128 * 128;
+    map.P = g.P;
+    map.n = g.n;
+    map.p = g.p;
+    map.q = g.q;
+    const int K = stage == 1 ? g.q : g.p;
+    if (K > 32) return cudaErrorInvalidValue;
+    const int npad = K <= 16 ? 16 : 32;
+    const int64_t ncols = stage == 1 ? g.L * g.p : map.Lpad * g.q;
+    const uint8_t *planes = (const uint8_t *)(stage == 1 ? t.fp8_s1 : t.fp8_s2);
+    size_t smem = fp8_smem_bytes(K, npad);
+    int64_t blocks = (ncols + 127) / 128;
+    if (blocks == 0) return cudaSuccess;
+    cudaError_t err;
+    if (npad == 16) {
+        err = cudaFuncSetAttribute(stage_fp8_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        stage_fp8_kernel<16><<<(unsigned)blocks, FP8_THREADS, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
+                                                                          ncols, K, K, in, out, status);
+    } else {
+        err = cudaFuncSetAttribute(stage_fp8_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        stage_fp8_kernel<32><<<(unsigned)blocks, FP8_THREADS, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
+                                                                          ncols, K, K, in, out, status);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace obfft

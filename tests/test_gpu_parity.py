@@ -13,7 +13,7 @@ from tests.helpers import bits_equal, mismatch_report, oracle_full
 
 pytestmark = pytest.mark.gpu
 
-OZAKI_MODES = ["int8"]
+OZAKI_MODES = ["fp8", "int8"]
 
 
 @pytest.fixture(scope="module", autouse=True)
