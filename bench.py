@@ -183,7 +183,7 @@ def main():
 
     n = args.size
     shape = (n, n, n)
-    mode = args.mode or "int8"
+    mode = args.mode or "fp8"
     x = S.complex_uniform(S.SEED_1024 + rank, shape, device="cuda")
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
@@ -234,7 +234,7 @@ def main():
 
     # comparator modes at the same size
     modes = {mode: ms_step}
-    others = [m for m in ("int8", "fp64") if m != mode]
+    others = [m for m in ("fp8", "int8", "fp64") if m != mode]
     for m in others:
         pl2, ms2 = time_mode(m, max(1, min(args.steps, 2)), 1)
         modes[m] = ms2 / max(1, min(args.steps, 2))
@@ -282,19 +282,29 @@ def main():
     c_epi = 203  # the paper's lower bound of integer instructions per output scalar
     alg_inst = 2 * c_epi * N3  # per stage launch: 2 scalar outputs per complex element
     achieved = alg_inst / (kern_ms * 1e-3) / 1e12
+    hbm_bytes = 32 * N3  # per stage launch: 16 B read + 16 B written per element
+    # tensor ops per stage launch (MAC = 2): FP8 mode issues 171 K=32 E4M3 MMAs per
+    # 4096 complex outputs (M=128 x N=32) plus Phase A (K=32 padded x N=48 FP16)
+    fp8_ops = 2 * N3 * (171 * 32 + 32 * 48)
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinst/s",
                 "frac": achieved / alu_peak, "traffic": None,
                 "kernel": f"stage_{mode}_kernel (axis 2, stage 1)", "kernel_ms": kern_ms,
-                "peak_note": "152 SMs x 4 x 32 lanes x max SM clock (derived)",
-                "hbm_frac_of_measured": (32 * N3 / (kern_ms * 1e-3) / 1e9) / peaks.get("hbm_gbs", 6791.0)}
+                "algorithmic": f"{2 * c_epi} integer instructions per complex output (paper c_epi = {c_epi} per scalar)",
+                "peak_note": "derived: 152 SMs x 4 schedulers x 32 lanes x max SM clock",
+                "hbm_frac_of_measured": (hbm_bytes / (kern_ms * 1e-3) / 1e9) / peaks.get("hbm_gbs", 6791.0),
+                "tensor_frac_of_measured_fp8": (fp8_ops / (kern_ms * 1e-3) / 1e12) / 4839.0 if mode == "fp8" else None,
+                "roof_ms_alu_hbm_tensor": [alg_inst / (alu_peak * 1e12) * 1e3,
+                                           hbm_bytes / (peaks.get("hbm_gbs", 6791.0) * 1e9) * 1e3,
+                                           fp8_ops / 4839e12 * 1e3]}
     cpu = None
     if not args.no_cpu and world == 1:
         cms, cores, sample = cpu_oracle_ms_per_transform(n, budget_s=12.0)
         cpu = {"value": cms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
-    launches = 6 * args.steps
+    launches = 6 * args.steps  # six stage kernels per 3-D transform
     line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp8": "e4m3", "int8": "s8", "fp64": "f64"}[mode],
             "data": "synthetic",
             "config": {"workload": f"{n}^3 complex128 forward 3-D FFT, splits 32x32 per axis",
                        "mode": mode, "seed": 20260003, "l2": "inputs larger than L2",
