@@ -137,6 +137,45 @@ obfft_status obfft_host_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int6
 obfft_status obfft_host_crt_constants(uint32_t *moduli, uint8_t *u_slices, uint8_t *w_slices,
                                       uint32_t *M4);
 
+/*
+ * Largest grid (n0 * n1 * n2 complex128 values) obfft_exec_fp64_noalloc accepts.
+ */
+#define OBFFT_NOALLOC_MAX_ELEMS (1 << 21)
+
+/*
+ * Forward or inverse 3-D transform that allocates no memory (the paper has no
+ * counterpart; this entry point exists for callers that are not allowed to
+ * allocate device memory while they run -- code where cudaMalloc/cudaFree are
+ * forbidden or where their implicit device synchronisation is unacceptable,
+ * or applications that hand a library only the buffers it works on).
+ *
+ * It runs the native-FP64 six-step path (the kernels of OBFFT_MODE_FP64_NATIVE
+ * plans, bit-identical results) on one n0 x n1 x n2 grid, with the stage-to-
+ * stage scratch and the twiddle tables in device memory that the library
+ * reserves at load time (file-scope device arrays, about 32 MiB per GPU that
+ * loads the library, held until the process exits).  in/out: device pointers
+ * to n0*n1*n2 complex128 values, 16-byte aligned, distinct.  dir = -1 forward,
+ * +1 inverse (unnormalised).  stream: a cudaStream_t (0 = default stream).
+ *
+ * Limits and behaviour:
+ *  - n0 * n1 * n2 <= OBFFT_NOALLOC_MAX_ELEMS, each axis p*q with p, q <= 64;
+ *    larger or unfactorable grids return OBFFT_ERR_UNSUPPORTED_SIZE.
+ *  - Calls no cudaMalloc, cudaFree or any allocating routine.  The first call
+ *    on a device looks up the device addresses of the reserved arrays
+ *    (cudaGetSymbolAddress, with that device current); with the CUDA driver's
+ *    lazy module loading this first call is also when the driver places the
+ *    arrays in device memory.  Make that first call during set-up, before any
+ *    stream capture; later calls leave free device memory unchanged.
+ *  - Every call on a device shares the same reserved arrays, which keep the
+ *    last call's contents.  Nothing in them needs to start at zero (the scratch
+ *    is fully written before it is read, the twiddles are rewritten by every
+ *    call).  Calls whose work overlaps on the GPU (e.g. on two streams) race
+ *    on these arrays and give wrong results: serialise them.
+ *  - The twiddle upload is a host-to-device copy from pageable memory.
+ */
+obfft_status obfft_exec_fp64_noalloc(const void *in, void *out, int64_t n0, int64_t n1, int64_t n2, int dir,
+                                     void *stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char *obfft_last_error(void);
 

@@ -29,7 +29,8 @@ MODES = {"fp8": OBFFT_MODE_FP8, "int8": OBFFT_MODE_INT8, "fp64": OBFFT_MODE_FP64
 # every symbol include/obfft.h declares
 EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_splits",
            "obfft_plan_create_many", "obfft_exec_many", "obfft_exec_stage", "obfft_last_error",
-           "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants")
+           "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants",
+           "obfft_exec_fp64_noalloc")
 
 _lib = None
 
@@ -67,6 +68,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_host_twiddle.restype = i32
     L.obfft_host_crt_constants.argtypes = [vp, vp, vp, vp]
     L.obfft_host_crt_constants.restype = i32
+    L.obfft_exec_fp64_noalloc.argtypes = [vp, vp, i64, i64, i64, i32, vp]
+    L.obfft_exec_fp64_noalloc.restype = i32
     _lib = L
     return L
 
@@ -115,6 +118,12 @@ def obfft_plan_get_splits(plan: int, grid: int, axis: int):
     p, q = ctypes.c_int(), ctypes.c_int()
     check(load().obfft_plan_get_splits(plan, grid, axis, ctypes.byref(p), ctypes.byref(q)))
     return p.value, q.value
+
+
+def obfft_exec_fp64_noalloc(in_ptr: int, out_ptr: int, n0: int, n1: int, n2: int, dir: int,
+                            stream: int = 0) -> None:
+    """Native-FP64 3-D transform that allocates nothing (scratch reserved at load)."""
+    check(load().obfft_exec_fp64_noalloc(in_ptr, out_ptr, n0, n1, n2, dir, stream))
 
 
 def obfft_last_error() -> str:

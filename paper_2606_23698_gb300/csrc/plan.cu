@@ -399,6 +399,16 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
     return OBFFT_OK;
 }
 
+// FP64 twiddles exp(dir 2 pi i m / N), m < N, rounded from double-double
+// (the values the FP64-native plans upload), for the no-allocation entry point.
+void fp64_twiddles(int N, int dir, double2 *out) {
+    for (int m = 0; m < N; m++) {
+        dd c, s;
+        dd_cos_sin_2pi(m, N, &c, &s);
+        out[m] = make_double2(c.hi, dir < 0 ? -s.hi : s.hi);
+    }
+}
+
 AxisTables *get_tables(obfft_plan P, int n, int pp, int qq, int dir) {
     for (auto &t : P->tables)
         if (t.n == n && t.p == pp && t.q == qq && t.dir == dir) return &t;
