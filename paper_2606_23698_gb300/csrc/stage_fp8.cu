@@ -215,22 +215,157 @@ __device__ __forceinline__ float canon(float x, float m, float im) {
     return r >= m ? r - m : r;
 }
 
+// ---------------------------------------------------------------------------
+// Kernel: 512 threads.  Thread (sub = warp % 4, qd = warp / 4) owns TMEM lane
+// c = 32 sub + lane (= DFT column c of the tile), deconstructs elements
+// [EPT qd, EPT qd + EPT) of that column and finishes outputs [OPT qd, OPT qd +
+// OPT) of every product.  The (modulus, product) steps are software
+// pipelined: the digits of step i+1 are generated (into the other TMEM
+// A-buffer) while the MMAs of step i run; TMEM accumulators and the TMA-loaded
+// constant planes are double buffered.
+// TMEM columns: accumulators [0,160) and [160,320), A digit planes [320,344)
+// and [344,368); Phase A reuses [0,480).
+// ---------------------------------------------------------------------------
+constexpr int FP8_WARPS = 16;
+constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 24;
+
 template <int NPAD>
-__global__ void __launch_bounds__(FP8_THREADS, 1)
+struct Fp8Cfg {
+    static constexpr int EPT = NPAD / 4;  // elements per thread (K <= NPAD)
+    static constexpr int OPT = NPAD / 4;  // outputs per thread per product
+    static constexpr int WPP = EPT / 4;   // 32-bit TMEM words per plane per thread
+};
+
+// digits of EPT balanced residues -> E4M3 words of up to 3 planes
+template <int KIND, int EPT>
+__device__ __forceinline__ void digits_to_words(const float (&v)[EPT], float s, uint32_t (&wd)[3][EPT / 4]) {
+#pragma unroll
+    for (int q4 = 0; q4 < EPT / 4; q4++) {
+        uint32_t pk[3][2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; h2++) {
+            float dg[3][2];
+#pragma unroll
+            for (int e2 = 0; e2 < 2; e2++) {
+                float x = v[q4 * 4 + h2 * 2 + e2];
+                if constexpr (KIND == KIND_SQ) {
+                    float h = rint_small(x * (1.0f / s));
+                    dg[0][e2] = h;
+                    dg[1][e2] = __fmaf_rn(-s, h, x);
+                    dg[2][e2] = 0.f;
+                } else if constexpr (KIND == KIND_B9) {
+                    float d1 = rint_small(x * 0.0625f);
+                    dg[1][e2] = d1;
+                    dg[0][e2] = __fmaf_rn(-16.0f, d1, x);
+                    dg[2][e2] = 0.f;
+                } else {
+                    float d2 = rint_small(x * 0.00390625f);
+                    float r = __fmaf_rn(-256.0f, d2, x);
+                    float d1 = rint_small(r * 0.0625f);
+                    dg[2][e2] = d2;
+                    dg[1][e2] = d1;
+                    dg[0][e2] = __fmaf_rn(-16.0f, d1, r);
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < 3; d++) pk[d][h2] = e4m3x2(dg[d][0], dg[d][1]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) wd[d][q4] = pk[d][0] | (pk[d][1] << 16);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void issue_products_ta(uint32_t dacc, uint32_t apl, uint32_t sBp, int npad,
+                                                  uint32_t idesc) {
+    const uint32_t planeB = (uint32_t)npad * 32;
+    auto mma = [&](int ci, int dj, int cls, uint32_t acc) {
+        uint64_t b = smem_desc(sBp + ci * planeB, 128, 256);
+        tc_mma_f8_ta(dacc + cls * npad, apl + dj * 8, b, idesc, acc);
+    };
+    if (KIND == KIND_SQ) {  // digits 0 = h, 1 = l
+        mma(0, 1, 1, 0);
+        mma(1, 0, 1, 1);
+        mma(1, 1, 0, 0);
+    } else if (KIND == KIND_B9) {
+        mma(0, 0, 0, 0);
+        mma(0, 1, 1, 0);
+        mma(1, 0, 1, 1);
+        mma(1, 1, 2, 0);
+    } else {
+        mma(0, 0, 0, 0);
+        mma(0, 1, 1, 0);
+        mma(1, 0, 1, 1);
+        mma(0, 2, 2, 0);
+        mma(1, 1, 2, 1);
+        mma(2, 0, 2, 1);
+        mma(1, 2, 3, 0);
+        mma(2, 1, 3, 1);
+        mma(2, 2, 4, 0);
+    }
+}
+
+// class accumulators of this thread's OPT outputs -> balanced residue mod m
+template <int KIND, int OPT>
+__device__ __forceinline__ void read_classes(uint32_t tacc, int npad, const ModConsts &mc, int k,
+                                             float (&out)[OPT]) {
+    constexpr int NC = KIND == KIND_B11 ? 5 : (KIND == KIND_SQ ? 2 : 3);
+    uint32_t r[NC][OPT];
+#pragma unroll
+    for (int cl = 0; cl < NC; cl++) {
+        if constexpr (OPT == 8) {
+            uint32_t t[8];
+            tmem_ld8(tacc + cl * npad, t);
+#pragma unroll
+            for (int i = 0; i < 8; i++) r[cl][i] = t[i];
+        } else {
+            uint32_t t[4];
+            tmem_ld4(tacc + cl * npad, t);
+#pragma unroll
+            for (int i = 0; i < 4; i++) r[cl][i] = t[i];
+        }
+    }
+    tmem_wait_ld();
+    float wts[5];
+    if constexpr (KIND == KIND_SQ) {
+        wts[0] = 1.f;
+        wts[1] = mc.fsq[k];
+    } else {
+        wts[0] = 1.f;
+        wts[1] = 16.f;
+        wts[2] = 256.f;
+        wts[3] = mc.fc3[k];
+        wts[4] = mc.fc4[k];
+    }
+    const float m = mc.fm[k], im = mc.finv[k];
+#pragma unroll
+    for (int i = 0; i < OPT; i++) {
+        float a = __uint_as_float(r[0][i]);
+#pragma unroll
+        for (int cl = 1; cl < NC; cl++) a = __fmaf_rn(wts[cl], __uint_as_float(r[cl][i]), a);
+        out[i] = __fmaf_rn(-m, rint_small(a * im), a);
+    }
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     stage_fp8_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab,
                      const ModConsts *__restrict__ gmc, ColMapT map, int64_t ncols, int K, int Kout,
                      const double2 *__restrict__ in, double2 *__restrict__ out, int *status) {
-    constexpr int NH = NPAD / 2;
+    using CF = Fp8Cfg<NPAD>;
+    constexpr int EPT = CF::EPT, OPT = CF::OPT, WPP = CF::WPP;
+    constexpr int NSTEP = 3 * NMOD;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ ModConsts mc;
-    __shared__ int colpart[2][128];
-    __shared__ __align__(8) uint64_t mbar[3];  // 0: B planes (TMA), 1: MMA, 2: Phase-A B (TMA)
+    __shared__ int colpart[4][128];
+    __shared__ __align__(8) uint64_t mbar[4];  // 0,1: B planes (TMA, per buffer), 2: MMA, 3: Phase-A B
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int c = 32 * (w & 3) + lane, hf = w >> 2;
-    const uint32_t lanebase = (uint32_t)(32 * (w & 3)) << 16;
+    const int sub = w & 3, qd = w >> 2;
+    const int c = 32 * sub + lane;
+    const uint32_t lanebase = (uint32_t)(32 * sub) << 16;
     const int64_t cbase = (int64_t)blockIdx.x * 128;
     const int64_t cg = cbase + c;
     const bool cvalid = map.valid(cg, ncols);
@@ -239,21 +374,17 @@ __global__ void __launch_bounds__(FP8_THREADS, 1)
     const uint32_t stage_rows = (uint32_t)Kout * 128;
     const uint32_t stage_bytes = (stage_rows >> 3) * PA_ROWB + 128;
     uint8_t *sStage = smem;
-    uint8_t *sA = smem + ((stage_bytes + 1023) & ~1023u);
-    uint8_t *sB = sA + 3 * 4096;
-    uint8_t *sPAB = sB + 9 * NPAD * 32;
+    uint8_t *sB0 = smem + ((stage_bytes + 1023) & ~1023u);
     const uint32_t planeB = NPAD * 32;
+    uint8_t *sPAB = sB0 + 2 * 9 * planeB;
     const uint8_t *gplanes = planes + (size_t)group * FP8_PLANES_PER_GROUP * planeB;
 
-    for (int i = tid; i < (int)(sizeof(ModConsts) / 4); i += FP8_THREADS)
+    for (int i = tid; i < (int)(sizeof(ModConsts) / 4); i += FP8_WARPS * 32)
         reinterpret_cast<uint32_t *>(&mc)[i] = reinterpret_cast<const uint32_t *>(gmc)[i];
-    // zero the staging tail (aliased K-chunk of the last row group)
     if (tid < 32) reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[tid] = 0u;
     if (tid == 0) {
         abort_flag = 0;
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
-        mbar_init(smem_u32(&mbar[2]), 1);
+        for (int b = 0; b < 4; b++) mbar_init(smem_u32(&mbar[b]), 1);
         mbar_fence_init();
     }
     if (w == 0) tmem_alloc(smem_u32(&tmem_holder), 512);
@@ -262,131 +393,191 @@ __global__ void __launch_bounds__(FP8_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
     if (tid == 0) {
-        mbar_expect_tx(smem_u32(&mbar[2]), PA_N * 64);
-        tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[2]));
-        uint32_t bytes0 = 3 * fp8_ndig(0) * planeB;
+        mbar_expect_tx(smem_u32(&mbar[3]), PA_N * 64);
+        tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[3]));
+        const uint32_t bytes0 = 3 * fp8_ndig(0) * planeB;
         mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
-        tma_bulk_g2s(smem_u32(sB), gplanes, bytes0, smem_u32(&mbar[0]));
+        tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
+    }
+    // K <= 16: bytes 16..31 of every A row stay zero (columns 4..7 of each plane)
+    if (NPAD == 16 && qd == 0) {
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                uint32_t ta = tmem + lanebase + APL_BASE + b * APL_COLS + d * 8 + 4;
+                tmem_st2(ta, 0u, 0u);
+                tmem_st2(ta + 2, 0u, 0u);
+            }
     }
 
-    // ---------------- deconstruction: x~ of this thread's 16 elements ----------------
-    uint64_t xb[16][2];
-    int lead = LEAD_ZERO;
+    // ---------------- deconstruction of this thread's EPT elements ----------------
+    Pieces pR[EPT], pI[EPT];
+    int e;
+    {
+        uint64_t xb[EPT][2];
+        int lead = LEAD_ZERO;
 #pragma unroll
-    for (int jj = 0; jj < 16; jj++) {
-        int j = 16 * hf + jj;
-        double2 x = make_double2(0.0, 0.0);
-        if (cvalid && j < K) x = in[map.in_index(cg, j)];
-        xb[jj][0] = (uint64_t)__double_as_longlong(x.x);
-        xb[jj][1] = (uint64_t)__double_as_longlong(x.y);
-        lead = max(lead, max(lead_exponent(xb[jj][0]), lead_exponent(xb[jj][1])));
-    }
-    colpart[hf][c] = lead;
-    __syncthreads();
-    int lead2 = max(colpart[0][c], colpart[1][c]);
-    const int e = lead2 == LEAD_ZERO ? 0 : lead2;
-    Pieces pR[16], pI[16];
-#pragma unroll
-    for (int jj = 0; jj < 16; jj++) {
-        pR[jj] = split_pieces(scale_round(xb[jj][0], e));
-        pI[jj] = split_pieces(scale_round(xb[jj][1], e));
-    }
-
-    uint32_t mma_phase = 0;
-    bool ok = true;
-    float Dp[NH], Ep[NH];
-    // ---------------- per modulus: digit planes, FP8 MMAs, residue epilogue ----------
-    for (int k = 0; k < NMOD && ok; k++) {
-        ok = mbar_wait(smem_u32(&mbar[0]), (uint32_t)(k & 1), WAIT_LIMIT);
-        const int kind = fp8_kind(k);
-        const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
-        const float mf = mc.fm[k], halfm = mc.fhalf[k], imf = mc.finv[k];
-        uint32_t rR[16], rI[16];
-#pragma unroll
-        for (int jj = 0; jj < 16; jj++) {
-            rR[jj] = residue(pR[jj], m, mu, c20, c40, cn);
-            rI[jj] = residue(pI[jj], m, mu, c20, c40, cn);
+        for (int jj = 0; jj < EPT; jj++) {
+            int j = EPT * qd + jj;
+            double2 x = make_double2(0.0, 0.0);
+            if (cvalid && j < K) x = in[map.in_index(cg, j)];
+            xb[jj][0] = (uint64_t)__double_as_longlong(x.x);
+            xb[jj][1] = (uint64_t)__double_as_longlong(x.y);
+            lead = max(lead, max(lead_exponent(xb[jj][0]), lead_exponent(xb[jj][1])));
         }
-        for (int p = 0; p < 3; p++) {
-            float v[16];
+        colpart[qd][c] = lead;
+        __syncthreads();
+        int l2 = max(max(colpart[0][c], colpart[1][c]), max(colpart[2][c], colpart[3][c]));
+        e = l2 == LEAD_ZERO ? 0 : l2;
 #pragma unroll
-            for (int jj = 0; jj < 16; jj++) {
-                uint32_t r = p == 0 ? rR[jj] : (p == 1 ? rI[jj] : rR[jj] + rI[jj]);
-                r = r >= m ? r - m : r;
-                float f = __uint_as_float(0x4B000000u | r) - 8388608.0f;  // exact r
-                v[jj] = f > halfm ? f - mf : f;                            // balanced
+        for (int jj = 0; jj < EPT; jj++) {
+            pR[jj] = split_pieces(scale_round(xb[jj][0], e));
+            pI[jj] = split_pieces(scale_round(xb[jj][1], e));
+        }
+    }
+
+    uint32_t rR[EPT], rI[EPT];
+    float Dp[OPT], Ep[OPT];
+    // digits of step i into A buffer (i & 1)
+    auto gen = [&](int i) {
+        const int k = i / 3, p = i % 3;
+        const uint32_t m = mc.m[k];
+        if (p == 0) {
+            const uint32_t mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
+#pragma unroll
+            for (int jj = 0; jj < EPT; jj++) {
+                rR[jj] = residue(pR[jj], m, mu, c20, c40, cn);
+                rI[jj] = residue(pI[jj], m, mu, c20, c40, cn);
             }
+        }
+        const float mf = mc.fm[k], halfm = mc.fhalf[k];
+        float v[EPT];
+#pragma unroll
+        for (int jj = 0; jj < EPT; jj++) {
+            uint32_t r = p == 0 ? rR[jj] : (p == 1 ? rI[jj] : rR[jj] + rI[jj]);
+            r = r >= m ? r - m : r;
+            float f = __uint_as_float(0x4B000000u | r) - 8388608.0f;
+            v[jj] = f > halfm ? f - mf : f;
+        }
+        uint32_t wd[3][WPP];
+        const int kind = fp8_kind(k);
+        if (kind == KIND_SQ)
+            digits_to_words<KIND_SQ, EPT>(v, mc.fsq[k], wd);
+        else if (kind == KIND_B9)
+            digits_to_words<KIND_B9, EPT>(v, 0.f, wd);
+        else
+            digits_to_words<KIND_B11, EPT>(v, 0.f, wd);
+        const uint32_t ta = tmem + lanebase + APL_BASE + (uint32_t)(i & 1) * APL_COLS + (uint32_t)(qd * WPP);
+        const int nd = fp8_ndig(k);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (d < nd) {
+                if constexpr (WPP == 2)
+                    tmem_st2(ta + d * 8, wd[d][0], wd[d][1]);
+                else
+                    tmem_st1(ta + d * 8, wd[d][0]);
+            }
+        }
+    };
+    // MMAs of step i (thread 0 only)
+    auto issue = [&](int i) -> bool {
+        const int k = i / 3, p = i % 3;
+        if (p == 0) {
+            if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
+            if (k + 1 < NMOD) {  // buffer (k+1)&1 was last read by modulus k-1, whose MMAs are done
+                const uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
+                mbar_expect_tx(smem_u32(&mbar[(k + 1) & 1]), bytes);
+                tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * 9 * planeB),
+                             gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes,
+                             smem_u32(&mbar[(k + 1) & 1]));
+            }
+        }
+        const uint32_t idesc = instr_desc(128, NPAD, 0);
+        const uint32_t sBp = smem_u32(sB0 + (k & 1) * 9 * planeB) + (uint32_t)(p * fp8_ndig(k)) * planeB;
+        const uint32_t dacc = tmem + (uint32_t)(i & 1) * ACC_COLS;
+        const uint32_t apl = tmem + APL_BASE + (uint32_t)(i & 1) * APL_COLS;
+        const int kind = fp8_kind(k);
+        if (kind == KIND_SQ)
+            issue_products_ta<KIND_SQ>(dacc, apl, sBp, NPAD, idesc);
+        else if (kind == KIND_B9)
+            issue_products_ta<KIND_B9>(dacc, apl, sBp, NPAD, idesc);
+        else
+            issue_products_ta<KIND_B11>(dacc, apl, sBp, NPAD, idesc);
+        tc_commit(smem_u32(&mbar[2]));
+        return true;
+    };
+
+    gen(0);
+    tmem_wait_st();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        tc_fence_after();
+        if (!issue(0)) abort_flag = 1;
+    }
+    __syncthreads();
+    bool ok = abort_flag == 0;
+    uint32_t mma_phase = 0;
+    for (int i = 0; i < NSTEP && ok; i++) {
+        if (i + 1 < NSTEP) gen(i + 1);
+        const bool okm = mbar_wait(smem_u32(&mbar[2]), mma_phase, WAIT_LIMIT);
+        mma_phase ^= 1;
+        tc_fence_after();
+        const int k = i / 3, p = i % 3;
+        if (okm) {
+            float res[OPT];
+            const uint32_t tacc = tmem + lanebase + (uint32_t)(i & 1) * ACC_COLS + (uint32_t)(qd * OPT);
+            const int kind = fp8_kind(k);
             if (kind == KIND_SQ)
-                write_digits<KIND_SQ>(v, sA, c, hf, mc.fsq[k]);
+                read_classes<KIND_SQ, OPT>(tacc, NPAD, mc, k, res);
             else if (kind == KIND_B9)
-                write_digits<KIND_B9>(v, sA, c, hf, 0.f);
+                read_classes<KIND_B9, OPT>(tacc, NPAD, mc, k, res);
             else
-                write_digits<KIND_B11>(v, sA, c, hf, 0.f);
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t idesc = instr_desc(128, NPAD, 0);
-                const uint32_t sBp = smem_u32(sB) + (uint32_t)(p * fp8_ndig(k)) * planeB;
-                if (kind == KIND_SQ)
-                    issue_products<KIND_SQ>(tmem, smem_u32(sA), sBp, NPAD, idesc);
-                else if (kind == KIND_B9)
-                    issue_products<KIND_B9>(tmem, smem_u32(sA), sBp, NPAD, idesc);
-                else
-                    issue_products<KIND_B11>(tmem, smem_u32(sA), sBp, NPAD, idesc);
-                tc_commit(smem_u32(&mbar[1]));
-            }
-            bool okm = mbar_wait(smem_u32(&mbar[1]), mma_phase, WAIT_LIMIT);
-            mma_phase ^= 1;
-            tc_fence_after();
-            float res[NH];
-            if (okm) {
-                if (kind == KIND_SQ)
-                    read_product<KIND_SQ, NH>(tmem + lanebase, NPAD, hf, mc, k, res);
-                else if (kind == KIND_B9)
-                    read_product<KIND_B9, NH>(tmem + lanebase, NPAD, hf, mc, k, res);
-                else
-                    read_product<KIND_B11, NH>(tmem + lanebase, NPAD, hf, mc, k, res);
-            } else {
-                atomicExch(&abort_flag, 1);
-            }
+                read_classes<KIND_B11, OPT>(tacc, NPAD, mc, k, res);
             if (p == 0) {
 #pragma unroll
-                for (int i = 0; i < NH; i++) Dp[i] = okm ? res[i] : 0.f;
+                for (int o = 0; o < OPT; o++) Dp[o] = res[o];
             } else if (p == 1) {
 #pragma unroll
-                for (int i = 0; i < NH; i++) Ep[i] = okm ? res[i] : 0.f;
-            } else if (okm) {
-                // Karatsuba combine in the residue domain, canonicalise, FP16 -> staging
+                for (int o = 0; o < OPT; o++) Ep[o] = res[o];
+            } else {
+                const float mf = mc.fm[k], imf = mc.finv[k];
 #pragma unroll
-                for (int i = 0; i < NH; i++) {
-                    int kout = hf * NH + i;
-                    if (kout >= Kout) continue;
-                    float Rv = canon(Dp[i] - Ep[i], mf, imf);
-                    float Iv = canon(res[i] - Dp[i] - Ep[i], mf, imf);
-                    uint32_t row = (uint32_t)kout * 128 + c;
-                    uint32_t hv = f16x2(Rv, Iv);  // exact: canonical residues < 2048
-                    *reinterpret_cast<uint16_t *>(sStage + stage_off(row, k)) = (uint16_t)(hv & 0xFFFFu);
-                    *reinterpret_cast<uint16_t *>(sStage + stage_off(row, 12 + k)) = (uint16_t)(hv >> 16);
+                for (int o = 0; o < OPT; o++) {
+                    const int kout = qd * OPT + o;
+                    if (kout < Kout) {
+                        float Rv = canon(Dp[o] - Ep[o], mf, imf);
+                        float Iv = canon(res[o] - Dp[o] - Ep[o], mf, imf);
+                        const uint32_t row = (uint32_t)kout * 128 + c;
+                        const uint32_t hv = f16x2(Rv, Iv);  // exact: canonical residues < 2048
+                        *reinterpret_cast<uint16_t *>(sStage + stage_off(row, k)) = (uint16_t)(hv & 0xFFFFu);
+                        *reinterpret_cast<uint16_t *>(sStage + stage_off(row, 12 + k)) = (uint16_t)(hv >> 16);
+                    }
                 }
             }
-            tc_fence_before();
-            __syncthreads();
-            if (abort_flag) ok = false;
+        } else {
+            atomicExch(&abort_flag, 1);
         }
-        if (ok && tid == 0 && k + 1 < NMOD) {
-            uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
-            mbar_expect_tx(smem_u32(&mbar[0]), bytes);
-            tma_bulk_g2s(smem_u32(sB), gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes,
-                         smem_u32(&mbar[0]));
+        tmem_wait_st();
+        tc_fence_before();
+        __syncthreads();
+        if (abort_flag) {
+            ok = false;
+            break;
         }
+        if (tid == 0 && i + 1 < NSTEP) {
+            tc_fence_after();
+            if (!issue(i + 1)) abort_flag = 1;
+        }
+        // an abort raised by issue() is seen after the next step's barrier
     }
 
     // ---------------- CRT Phase A on FP16 tensor cores, then Kulisch + lift + pack ----
     if (ok) {
         fence_async_smem();
         __syncthreads();
-        ok = mbar_wait(smem_u32(&mbar[2]), 0, WAIT_LIMIT);
+        ok = mbar_wait(smem_u32(&mbar[3]), 0, WAIT_LIMIT);
         const uint32_t idescA = instr_desc(128, PA_N, 0);
         const int per_wave = 10;
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
@@ -400,16 +591,16 @@ __global__ void __launch_bounds__(FP8_THREADS, 1)
                     tc_mma_f16(d, smem_desc(aaddr + 256, 128, PA_ROWB), smem_desc(smem_u32(sPAB) + 256, 128, 512),
                                idescA, 1);
                 }
-                tc_commit(smem_u32(&mbar[1]));
+                tc_commit(smem_u32(&mbar[2]));
             }
-            bool okm = mbar_wait(smem_u32(&mbar[1]), mma_phase, WAIT_LIMIT);
+            bool okm = mbar_wait(smem_u32(&mbar[2]), mma_phase, WAIT_LIMIT);
             mma_phase ^= 1;
             tc_fence_after();
             if (okm) {
-                for (int bi = hf; bi < nb; bi += 2) {
+                for (int bi = qd; bi < nb; bi += 4) {
                     const int kout = b0 + bi;
                     uint32_t r0[16], r1[16], r2[16];
-                    uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
+                    const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
                     tmem_ld16(ta, r0);
                     tmem_ld16(ta + 16, r1);
                     tmem_ld16(ta + 32, r2);
@@ -454,8 +645,7 @@ __global__ void __launch_bounds__(FP8_THREADS, 1)
     }
     if (!ok && tid == 0) {
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
-        // give in-flight tensor-core work a bounded chance to drain before freeing TMEM
-        mbar_wait(smem_u32(&mbar[1]), mma_phase, WAIT_LIMIT);
+        mbar_wait(smem_u32(&mbar[2]), mma_phase, WAIT_LIMIT);  // let in-flight MMAs drain (bounded)
     }
     tc_fence_before();
     __syncthreads();
@@ -464,7 +654,7 @@ __global__ void __launch_bounds__(FP8_THREADS, 1)
 
 size_t fp8_smem_bytes(int Kout, int npad) {
     size_t stage_bytes = (size_t)Kout * 128 / 8 * PA_ROWB + 128;
-    return ((stage_bytes + 1023) & ~(size_t)1023) + 3 * 4096 + 9 * (size_t)npad * 32 + PA_N * 64;
+    return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * 9 * (size_t)npad * 32 + PA_N * 64;
 }
 
 cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
@@ -489,12 +679,12 @@ cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const vo
     if (npad == 16) {
         err = cudaFuncSetAttribute(stage_fp8_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp8_kernel<16><<<(unsigned)blocks, FP8_THREADS, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
+        stage_fp8_kernel<16><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
                                                                           ncols, K, K, in, out, status);
     } else {
         err = cudaFuncSetAttribute(stage_fp8_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp8_kernel<32><<<(unsigned)blocks, FP8_THREADS, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
+        stage_fp8_kernel<32><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
                                                                           ncols, K, K, in, out, status);
     }
     return cudaGetLastError();
