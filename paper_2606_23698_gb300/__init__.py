@@ -11,3 +11,4 @@ from ._lib import (OBFFT_MODE_FP8, OBFFT_MODE_INT8, OBFFT_MODE_FP64_NATIVE, MODE
                    obfft_exec_many, obfft_exec_stage, obfft_destroy, obfft_plan_get_splits,
                    obfft_last_error, obfft_version)
 from .api import Plan, PlanMany, fft3, ifft3  # noqa: F401
+from .autograd import ObFFT3, fft3_autograd  # noqa: F401
