@@ -37,6 +37,7 @@ def parse():
     ap.add_argument("--size", type=int, default=1024, help="cube edge (debug only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the side configurations")
     return ap.parse_args()
 
 
@@ -157,6 +158,80 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- side configurations --
+def side_configs(torch, Plan, PlanMany, S, mode):
+    """The other workloads of the benchmark set, measured at their own sizes:
+    wide-range 256^3 (errors per mode, round trip), the 40-grid uneven batch
+    (one captured graph), and the 8 x 128^3 differentiable transform."""
+    from paper_2606_23698_gb300 import fft3_autograd
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # 256^3, magnitudes 2^U(-30,30), forward then inverse, all modes
+    n = 256
+    x = S.complex_wide_range(S.SEED_256_WIDE, (n, n, n), device="cuda")
+    y64 = Plan(n, n, n, mode="fp64").exec(x, dir=-1)
+    res = {}
+    for m in ("fp8", "int8", "fp64"):
+        pl = Plan(n, n, n, mode=m)
+        y = pl.exec(x, dir=-1)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        y = pl.exec(x, dir=-1)
+        b.record()
+        torch.cuda.synchronize()
+        back = pl.exec(y, dir=+1) / (n ** 3)
+        res[m] = {"fwd_ms": a.elapsed_time(b),
+                  "rel_diff_vs_fp64": float(torch.linalg.vector_norm(y - y64) / torch.linalg.vector_norm(y64)),
+                  "roundtrip_rel_err": float(torch.linalg.vector_norm(back - x) / torch.linalg.vector_norm(x))}
+        pl.close()
+    out["wide_range_256cube"] = res
+    del x, y64
+    # uneven batch: 16 x 64^3, 12 x 96x128x128, 8 x 192^3, 4 x 256x256x384, N(0,1)
+    dims = S.UNEVEN_BATCH
+    xs = [S.complex_gaussian(S.SEED_UNEVEN + i, d, device="cuda") for i, d in enumerate(dims)]
+    outs = [torch.empty_like(t) for t in xs]
+    pm = PlanMany(dims, mode=mode)
+    pm.exec(xs, outs)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(3):
+        pm.exec(xs, outs)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 3
+    out["uneven_batch_40_grids"] = {"mode": mode, "ms": ms, "grids_per_s": len(dims) / (ms * 1e-3),
+                                    "elements": int(sum(d[0] * d[1] * d[2] for d in dims)),
+                                    "execution": "one CUDA graph launch per call"}
+    pm.close()
+    del xs, outs
+    # differentiable transform: 8 x 128^3, loss = sum |F(x) w|^2, forward + backward
+    xg = S.complex_uniform(S.SEED_GRAD, (8, 128, 128, 128), device="cuda")
+    w = S.spectral_mask(S.SEED_GRAD, (8, 128, 128, 128), device="cuda")
+    grad = {}
+    for m in (mode, "fp64"):
+        xr = xg.clone().requires_grad_(True)
+        loss = (torch.abs(fft3_autograd(xr, m) * w) ** 2).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        xr = xg.clone().requires_grad_(True)
+        a.record()
+        loss = (torch.abs(fft3_autograd(xr, m) * w) ** 2).sum()
+        loss.backward()
+        b.record()
+        torch.cuda.synchronize()
+        grad[m] = {"fwd_bwd_ms": a.elapsed_time(b)}
+        grad[m]["_g"] = xr.grad
+    grad[mode]["grad_rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(grad[mode]["_g"] - grad["fp64"]["_g"]) /
+                                              torch.linalg.vector_norm(grad["fp64"]["_g"]))
+    for m in grad:
+        grad[m].pop("_g")
+    out["autograd_8x128cube"] = grad
+    return out
+
+
 # --------------------------------------------------------------- our arm ----
 def main():
     args = parse()
@@ -178,7 +253,7 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2606_23698_gb300 import Plan, _lib
+    from paper_2606_23698_gb300 import Plan, PlanMany, _lib
     from synth import inputs as S
 
     n = args.size
@@ -268,6 +343,12 @@ def main():
         e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
         del hx, hy, dx
 
+    extra = None
+    if not args.no_extra and rank == 0 and n == 1024:
+        del y_main
+        torch.cuda.empty_cache()
+        extra = side_configs(torch, Plan, PlanMany, S, mode)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -311,7 +392,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "gflops_5nlogn": gflops, "modes_ms": modes, "rel_diff_vs_fp64_native": diff,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches}
+            "gpu_launches": launches, "side_configs": extra}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -133,4 +133,113 @@ __device__ __forceinline__ i128 lift_two_sided(u128 E, int64_t zhat, const ModCo
     return R;
 }
 
+// ---------------------------------------------------------------------------
+// Lean Kulisch finish for the FP8 path (Algorithm 2), from the 21 FP32 Phase-A
+// accumulators of one scalar output, each holding 2^23 + P_s (s < 15) or
+// 2^23 + Q_t (t < 6) so that its bit pattern is 0x4B000000 + P (P < 2^23).
+//   E = sum_s P_s 256^s (mod 2^128)       -- 15 wide multiply-adds
+//   z_acc = sum_t Q_t 256^t (mod 2^64)    -- exact, z_acc < 2^63
+//   zhat = floor((z_acc + 2^47) / 2^48);  R = E - zhat M  (mod 2^128)
+// The two-sided correction is only needed when z_acc / 2^48 lies within 2^-33
+// of a rounding boundary (the lift error is below 2^-34 for canonical
+// residues); that rare case, and results that would be subnormal or overflow,
+// take the general 128-bit path.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double kulisch_pack_fp8(const uint32_t *wv, const ModConsts &mc, int et,
+                                                   const uint32_t (&ebias)[4], uint64_t zbias) {
+    uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    a0 += (uint64_t)wv[0];
+    a0 += (uint64_t)wv[1] * 256u;
+    a0 += (uint64_t)wv[2] * 65536u;
+    a0 += (uint64_t)wv[3] * 16777216u;
+    a1 += (uint64_t)wv[4];
+    a1 += (uint64_t)wv[5] * 256u;
+    a1 += (uint64_t)wv[6] * 65536u;
+    a1 += (uint64_t)wv[7] * 16777216u;
+    a2 += (uint64_t)wv[8];
+    a2 += (uint64_t)wv[9] * 256u;
+    a2 += (uint64_t)wv[10] * 65536u;
+    a2 += (uint64_t)wv[11] * 16777216u;
+    a3 += (uint64_t)wv[12];
+    a3 += (uint64_t)wv[13] * 256u;
+    a3 += (uint64_t)wv[14] * 65536u;
+    // 128-bit words of the biased sum, then remove the constant bias
+    uint32_t w0 = (uint32_t)a0;
+    uint64_t t = (a0 >> 32) + a1;
+    uint32_t w1 = (uint32_t)t;
+    t = (t >> 32) + a2;
+    uint32_t w2 = (uint32_t)t;
+    t = (t >> 32) + a3;
+    uint32_t w3 = (uint32_t)t;
+    uint64_t z = (uint64_t)wv[15] + (uint64_t)wv[16] * 256u + (uint64_t)wv[17] * 65536u +
+                 (uint64_t)wv[18] * 16777216u + ((uint64_t)wv[19] << 32) + ((uint64_t)wv[20] << 40);
+    z -= zbias;
+    const uint64_t zr = z + (1ull << 47);
+    const uint32_t zhat = (uint32_t)(zr >> 48);
+    const uint64_t frac = zr & ((1ull << 48) - 1);
+    // R = E - bias - zhat M  (mod 2^128)
+    uint64_t p0 = (uint64_t)zhat * mc.M32[0];
+    uint64_t p1 = (uint64_t)zhat * mc.M32[1] + (p0 >> 32);
+    uint64_t p2 = (uint64_t)zhat * mc.M32[2] + (p1 >> 32);
+    uint32_t p3 = zhat * mc.M32[3] + (uint32_t)(p2 >> 32);
+    uint32_t s0, s1, s2, s3;
+    {
+        // s = zhat M + bias (128-bit add), then r = w - s
+        asm("add.cc.u32 %0, %4, %8;\n\taddc.cc.u32 %1, %5, %9;\n\taddc.cc.u32 %2, %6, %10;\n\taddc.u32 %3, %7, %11;"
+            : "=r"(s0), "=r"(s1), "=r"(s2), "=r"(s3)
+            : "r"((uint32_t)p0), "r"((uint32_t)p1), "r"((uint32_t)p2), "r"(p3), "r"(ebias[0]), "r"(ebias[1]),
+              "r"(ebias[2]), "r"(ebias[3]));
+    }
+    uint32_t r0, r1, r2, r3;
+    asm("sub.cc.u32 %0, %4, %8;\n\tsubc.cc.u32 %1, %5, %9;\n\tsubc.cc.u32 %2, %6, %10;\n\tsubc.u32 %3, %7, %11;"
+        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(w0), "r"(w1), "r"(w2), "r"(w3), "r"(s0), "r"(s1), "r"(s2), "r"(s3));
+    const bool near = frac < (1ull << 15) || frac >= (1ull << 48) - (1ull << 15);
+    if (near) {
+        i128 R = (i128)((((u128)r3) << 96) | (((u128)r2) << 64) | (((u128)r1) << 32) | (u128)r0);
+        u128 M = u128_from_words(mc.M32);
+        i128 half = (i128)u128_from_words(mc.halfM32);
+        if (R >= half) R -= (i128)M;
+        if (R < -half) R += (i128)M;
+        return pack_rne(R, et);
+    }
+    // fast pack: |R| < 2^117, normal result
+    const bool neg = (int32_t)r3 < 0;
+    if (neg) {
+        asm("sub.cc.u32 %0, 0, %0;\n\tsubc.cc.u32 %1, 0, %1;\n\tsubc.cc.u32 %2, 0, %2;\n\tsubc.u32 %3, 0, %3;"
+            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3));
+    }
+    uint64_t hi = ((uint64_t)r3 << 32) | r2, lo = ((uint64_t)r1 << 32) | r0;
+    uint64_t top;
+    bool sticky;
+    int L;
+    if (hi) {
+        int lz = __clzll((long long)hi);
+        top = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+        sticky = (lo << lz) != 0;
+        L = 128 - lz;
+    } else {
+        if (lo == 0) return 0.0;
+        int lz = __clzll((long long)lo);
+        top = lo << lz;
+        sticky = false;
+        L = 64 - lz;
+    }
+    uint64_t mant = top >> 11;
+    const uint32_t rbit = (uint32_t)(top >> 10) & 1u;
+    sticky = sticky || (top & 0x3FFull);
+    mant += rbit & (uint32_t)(sticky | (mant & 1));
+    int E2 = L - 53 + et + 1075;  // biased exponent of the result
+    if (mant >> 53) {
+        mant >>= 1;
+        E2 += 1;
+    }
+    if (E2 < 1 || E2 > 2046) {  // subnormal or overflow: general path
+        i128 R = (i128)((((u128)r3) << 96) | (((u128)r2) << 64) | (((u128)r1) << 32) | (u128)r0);
+        return pack_rne(neg ? -R : R, et);
+    }
+    const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)E2 << 52) | (mant & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
 }  // namespace obfft

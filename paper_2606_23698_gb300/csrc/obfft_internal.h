@@ -40,6 +40,10 @@ struct ModConsts {
     float fsq[NMOD];   // s for m = s^2, else 0
     float fc3[NMOD];   // 16^3 mod m
     float fc4[NMOD];   // 16^4 mod m
+    // Kulisch deposit biases of the FP32-bit-pattern deposits:
+    // sum_{s<15} 0x4B000000 * 256^s mod 2^128 and sum_{t<6} 0x4B000000 * 256^t mod 2^64
+    uint32_t kbias[4];
+    uint32_t zbias[2];
 };
 
 // Host-side constant generation (plan.cpp).
@@ -85,6 +89,14 @@ struct obfft_plan_s {
     obfft::ModConsts *d_consts = nullptr;
     void *d_pab = nullptr;     // Phase A B-matrix (FP16 u_k / w_k byte slices)
     int *d_status = nullptr;   // device status word (bounded-wait timeouts)
+    // multi-grid execution: the whole launch sequence captured once per
+    // (input pointers, output pointers, direction) and replayed as one graph
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    std::vector<const void *> graph_ins;
+    std::vector<void *> graph_outs;
+    int graph_dir = 0;
+    std::vector<void *> grid_scratch;  // scratch of grid g (offsets into `scratch`)
 };
 
 namespace obfft {

@@ -87,6 +87,13 @@ void make_mod_consts(ModConsts *mc) {
         mc->M32[w] = (uint32_t)(M >> (32 * w));
         mc->halfM32[w] = (uint32_t)((M >> 1) >> (32 * w));
     }
+    u128 kb = 0;
+    for (int s = 0; s < S_RAW; s++) kb += (u128)0x4B000000u << (8 * s);  // wraps mod 2^128
+    for (int w = 0; w < 4; w++) mc->kbias[w] = (uint32_t)(kb >> (32 * w));
+    uint64_t zb = 0;
+    for (int t = 0; t < S_FRAC; t++) zb += (uint64_t)0x4B000000u << (8 * t);  // mod 2^64
+    mc->zbias[0] = (uint32_t)zb;
+    mc->zbias[1] = (uint32_t)(zb >> 32);
 }
 
 // --------------------------------------------------- double-double sin / cos
@@ -446,7 +453,89 @@ static void free_tables(obfft_plan P) {
 
 using namespace obfft;
 
+// ------------------------------------------------------------------ autotune
+// With OBFFT_AUTOTUNE=1 in the environment, plan creation times every Bailey
+// split n = p * q (p, q within the mode's limit) of each distinct axis length on
+// a synthetic batch of lines (stage 1 + stage 2 launches, CUDA events, best of
+// 3 after a warm-up) and keeps the fastest.  Results remain exact for the
+// chosen split; the oracle reads the split back through obfft_plan_get_splits.
+static float time_split(obfft_plan P, int n, int pp, int qq, double2 *buf, double2 *tmp, double2 *outb,
+                        int64_t lines) {
+    AxisTables t;
+    t.n = n; t.p = pp; t.q = qq; t.dir = -1;
+    if (build_tables(P, t) != OBFFT_OK) return 1e30f;
+    StageGeom g;
+    g.L = lines; g.P = lines; g.n = n; g.p = pp; g.q = qq;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(a, 0);
+        for (int st = 1; st <= 2; st++) {
+            const double2 *src = st == 1 ? buf : tmp;
+            double2 *dst = st == 1 ? tmp : outb;
+            if (P->mode == OBFFT_MODE_INT8) launch_stage_int8(t, P->d_consts, g, st, src, dst, 0);
+            else if (P->mode == OBFFT_MODE_FP8) launch_stage_fp8(t, P->d_consts, P->d_pab, P->d_status, g, st, src, dst, 0);
+            else launch_stage_fp64(t, g, st, src, dst, 0);
+        }
+        cudaEventRecord(b, 0);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(t.int8_s1); cudaFree(t.int8_s2); cudaFree(t.fp8_s1); cudaFree(t.fp8_s2); cudaFree(t.tw);
+    return best;
+}
+
+static void autotune_splits(obfft_plan P) {
+    const char *env = getenv("OBFFT_AUTOTUNE");
+    if (!env || env[0] != '1') return;
+    const int kmax = P->mode == OBFFT_MODE_FP8 ? 32 : KMAX;
+    std::map<int, std::pair<int, int>> best;
+    for (auto &gd : P->grids)
+        for (int a = 0; a < 3; a++) {
+            const int n = (int)gd.n[a];
+            if (n == 1 || best.count(n)) continue;
+            const int64_t lines = std::max<int64_t>(256, ((int64_t)1 << 21) / n);
+            double2 *buf = nullptr, *tmp = nullptr, *outb = nullptr;
+            size_t bytes = (size_t)lines * n * 16;
+            if (cudaMalloc(&buf, bytes) != cudaSuccess || cudaMalloc(&tmp, bytes) != cudaSuccess ||
+                cudaMalloc(&outb, bytes) != cudaSuccess) {
+                cudaFree(buf); cudaFree(tmp); cudaFree(outb);
+                return;
+            }
+            cudaMemset(buf, 0, bytes);
+            float tbest = 1e30f;
+            std::pair<int, int> pick(gd.ax[a].p, gd.ax[a].q);
+            for (int q = 1; q <= n; q++) {
+                if (n % q) continue;
+                int p = n / q;
+                if (p > kmax || q > kmax) continue;
+                float tm = time_split(P, n, p, q, buf, tmp, outb, lines);
+                if (tm < tbest) {
+                    tbest = tm;
+                    pick = {p, q};
+                }
+            }
+            cudaFree(buf); cudaFree(tmp); cudaFree(outb);
+            best[n] = pick;
+        }
+    for (auto &gd : P->grids)
+        for (int a = 0; a < 3; a++) {
+            auto it = best.find((int)gd.n[a]);
+            if (it != best.end()) {
+                gd.ax[a].p = it->second.first;
+                gd.ax[a].q = it->second.second;
+            }
+        }
+}
+
 static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
+    autotune_splits(P);
     // tables for both directions of every distinct axis
     for (auto &gd : P->grids)
         for (int a = 0; a < 3; a++) {
@@ -466,15 +555,27 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
                 }
             }
         }
-    size_t maxel = 0;
-    for (auto &gd : P->grids) maxel = std::max(maxel, (size_t)(gd.n[0] * gd.n[1] * gd.n[2]));
-    P->scratch_bytes = maxel * (size_t)P->batch * 16;
+    size_t maxel = 0, sumel = 0;
+    for (auto &gd : P->grids) {
+        maxel = std::max(maxel, (size_t)(gd.n[0] * gd.n[1] * gd.n[2]));
+        sumel += (size_t)(gd.n[0] * gd.n[1] * gd.n[2]);
+    }
+    // single grid: one grid-sized scratch; several grids: one slice per grid so
+    // that their launch chains do not share memory
+    P->scratch_bytes = (P->grids.size() == 1 ? maxel * (size_t)P->batch : sumel) * 16;
     cudaError_t e = cudaMalloc(&P->scratch, P->scratch_bytes ? P->scratch_bytes : 16);
     if (e != cudaSuccess) {
         free_tables(P);
         cudaFree(P->d_consts);
         delete P;
         return set_error(OBFFT_ERR_ALLOC, std::string("scratch: ") + cudaGetErrorString(e));
+    }
+    if (P->grids.size() > 1) {
+        size_t off = 0;
+        for (auto &gd : P->grids) {
+            P->grid_scratch.push_back((char *)P->scratch + off * 16);
+            off += (size_t)(gd.n[0] * gd.n[1] * gd.n[2]);
+        }
     }
     *out = P;
     return OBFFT_OK;
@@ -557,6 +658,8 @@ extern "C" obfft_status obfft_destroy(obfft_plan p) {
     cudaGetDevice(&cur);
     cudaSetDevice(p->device);
     free_tables(p);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     cudaFree(p->scratch);
     cudaFree(p->d_consts);
     cudaFree(p->d_pab);
@@ -605,9 +708,9 @@ static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, i
 }
 
 static obfft_status exec_grid(obfft_plan P, const GridDesc &gd, int64_t batch, const double2 *in,
-                              double2 *out, int dir, cudaStream_t s) {
+                              double2 *out, int dir, cudaStream_t s, double2 *scratch_override = nullptr) {
     const double2 *src = in;
-    double2 *scratch = (double2 *)P->scratch;
+    double2 *scratch = scratch_override ? scratch_override : (double2 *)P->scratch;
     const int64_t total = gd.n[0] * gd.n[1] * gd.n[2] * batch;
     for (int axis = 2; axis >= 0; axis--) {
         const AxisPlan &ap = gd.ax[axis];
@@ -651,19 +754,56 @@ extern "C" obfft_status obfft_exec(obfft_plan p, const void *in, void *out, int 
     return exec_grid(p, p->grids[0], p->batch, (const double2 *)in, (double2 *)out, dir, (cudaStream_t)stream);
 }
 
+// Multi-grid execution (the uneven batch).  Every grid gets its own slice of
+// the plan scratch, so the grids' launch chains are independent; the whole
+// sequence is captured once into a CUDA graph for a given set of pointers and
+// direction, and later calls with the same arguments replay it with one
+// cudaGraphLaunch on the caller's stream.
 extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, void *const *outs, int dir,
                                         void *stream) {
     if (!p || !ins || !outs) return set_error(OBFFT_ERR_ARG, "NULL argument");
     if (dir != -1 && dir != 1) return set_error(OBFFT_ERR_ARG, "dir must be -1 or +1");
-    for (size_t g = 0; g < p->grids.size(); g++) {
+    const size_t G = p->grids.size();
+    for (size_t g = 0; g < G; g++) {
         obfft_status st = check_ptrs(ins[g], outs[g]);
         if (st != OBFFT_OK) return st;
     }
-    for (size_t g = 0; g < p->grids.size(); g++) {
-        obfft_status st = exec_grid(p, p->grids[g], 1, (const double2 *)ins[g], (double2 *)outs[g], dir,
-                                    (cudaStream_t)stream);
-        if (st != OBFFT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    bool same = p->graph_exec && p->graph_dir == dir && p->graph_ins.size() == G;
+    for (size_t g = 0; same && g < G; g++) same = p->graph_ins[g] == ins[g] && p->graph_outs[g] == outs[g];
+    if (!same) {
+        if (p->graph_exec) {
+            cudaGraphExecDestroy(p->graph_exec);
+            p->graph_exec = nullptr;
+        }
+        cudaError_t e = cudaSuccess;
+        if (!p->capture_stream) e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
+        e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        obfft_status st = OBFFT_OK;
+        for (size_t g = 0; g < G && st == OBFFT_OK; g++)
+            st = exec_grid(p, p->grids[g], 1, (const double2 *)ins[g], (double2 *)outs[g], dir, p->capture_stream,
+                           (double2 *)p->grid_scratch[g]);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(p->capture_stream, &graph);
+        if (st != OBFFT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e2 != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("capture end: ") + cudaGetErrorString(e2));
+        e2 = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e2 != cudaSuccess) {
+            p->graph_exec = nullptr;
+            return set_error(OBFFT_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+        }
+        p->graph_ins.assign(ins, ins + G);
+        p->graph_outs.assign(outs, outs + G);
+        p->graph_dir = dir;
     }
+    cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
+    if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
     return OBFFT_OK;
 }
 

@@ -82,6 +82,24 @@ struct ColMapT {
         return (b * n + k2 + (int64_t)q * k) * P + r;
     }
     __device__ __forceinline__ int group(int64_t c) const { return stage == 1 ? 0 : (int)(c / Lpad); }
+    // element j of column c lives at ibase + j * istride; output k at obase + k * ostride
+    __device__ __forceinline__ void strides(int64_t c, int64_t &ibase, int64_t &istride, int64_t &obase,
+                                            int64_t &ostride) const {
+        if (stage == 1) {
+            int64_t l = c / p, j1 = c - l * p;
+            ibase = l * n + j1;
+            istride = p;
+            obase = ibase;
+            ostride = p;
+        } else {
+            int64_t k2 = c / Lpad, l = c - k2 * Lpad;
+            int64_t b = l / P, r = l - b * P;
+            ibase = l * n + k2 * p;
+            istride = 1;
+            obase = (b * n + k2) * P + r;
+            ostride = (int64_t)q * P;
+        }
+    }
 };
 
 // byte offset of element (row, k) of the Phase-A staging (K-major, 3 chunks of 8 f16)
@@ -223,11 +241,12 @@ __device__ __forceinline__ float canon(float x, float m, float im) {
 // pipelined: the digits of step i+1 are generated (into the other TMEM
 // A-buffer) while the MMAs of step i run; TMEM accumulators and the TMA-loaded
 // constant planes are double buffered.
-// TMEM columns: accumulators [0,160) and [160,320), A digit planes [320,344)
-// and [344,368); Phase A reuses [0,480).
+// TMEM columns: accumulators [0,160) and [160,320), A digit planes in three
+// buffers [320,344), [344,368), [368,392); Phase A reuses [0,480).  Two MMA
+// steps are in flight while a third step's digits are generated.
 // ---------------------------------------------------------------------------
 constexpr int FP8_WARPS = 16;
-constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 24;
+constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 24, N_ABUF = 3;
 
 template <int NPAD>
 struct Fp8Cfg {
@@ -358,7 +377,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ ModConsts mc;
     __shared__ int colpart[4][128];
-    __shared__ __align__(8) uint64_t mbar[4];  // 0,1: B planes (TMA, per buffer), 2: MMA, 3: Phase-A B
+    __shared__ __align__(8) uint64_t mbar[5];  // 0,1: B planes (TMA, per buffer), 2,3: MMA, 4: Phase-A B
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
@@ -384,7 +403,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     if (tid < 32) reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[tid] = 0u;
     if (tid == 0) {
         abort_flag = 0;
-        for (int b = 0; b < 4; b++) mbar_init(smem_u32(&mbar[b]), 1);
+        for (int b = 0; b < 5; b++) mbar_init(smem_u32(&mbar[b]), 1);
         mbar_fence_init();
     }
     if (w == 0) tmem_alloc(smem_u32(&tmem_holder), 512);
@@ -393,8 +412,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
     if (tid == 0) {
-        mbar_expect_tx(smem_u32(&mbar[3]), PA_N * 64);
-        tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[3]));
+        mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
+        tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
         const uint32_t bytes0 = 3 * fp8_ndig(0) * planeB;
         mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
         tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
@@ -402,7 +421,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // K <= 16: bytes 16..31 of every A row stay zero (columns 4..7 of each plane)
     if (NPAD == 16 && qd == 0) {
 #pragma unroll
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < (int)N_ABUF; b++)
 #pragma unroll
             for (int d = 0; d < 3; d++) {
                 uint32_t ta = tmem + lanebase + APL_BASE + b * APL_COLS + d * 8 + 4;
@@ -414,6 +433,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // ---------------- deconstruction of this thread's EPT elements ----------------
     Pieces pR[EPT], pI[EPT];
     int e;
+    int64_t ibase, istride, obase, ostride;
+    map.strides(cg, ibase, istride, obase, ostride);
     {
         uint64_t xb[EPT][2];
         int lead = LEAD_ZERO;
@@ -421,7 +442,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         for (int jj = 0; jj < EPT; jj++) {
             int j = EPT * qd + jj;
             double2 x = make_double2(0.0, 0.0);
-            if (cvalid && j < K) x = in[map.in_index(cg, j)];
+            if (cvalid && j < K) x = in[ibase + (int64_t)j * istride];
             xb[jj][0] = (uint64_t)__double_as_longlong(x.x);
             xb[jj][1] = (uint64_t)__double_as_longlong(x.y);
             lead = max(lead, max(lead_exponent(xb[jj][0]), lead_exponent(xb[jj][1])));
@@ -437,28 +458,32 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         }
     }
 
-    uint32_t rR[EPT], rI[EPT];
+    float vR[EPT], vI[EPT];
     float Dp[OPT], Ep[OPT];
-    // digits of step i into A buffer (i & 1)
+    // digits of step i into A buffer (i % 3)
     auto gen = [&](int i) {
         const int k = i / 3, p = i % 3;
-        const uint32_t m = mc.m[k];
-        if (p == 0) {
-            const uint32_t mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
+        const float mf = mc.fm[k], imf = mc.finv[k];
+        if (p == 0) {  // balanced residues of x~_R and x~_I for modulus k
+            const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
+            const float halfm = mc.fhalf[k];
 #pragma unroll
             for (int jj = 0; jj < EPT; jj++) {
-                rR[jj] = residue(pR[jj], m, mu, c20, c40, cn);
-                rI[jj] = residue(pI[jj], m, mu, c20, c40, cn);
+                float fr = __uint_as_float(0x4B000000u | residue(pR[jj], m, mu, c20, c40, cn)) - 8388608.0f;
+                float fi = __uint_as_float(0x4B000000u | residue(pI[jj], m, mu, c20, c40, cn)) - 8388608.0f;
+                vR[jj] = fr > halfm ? fr - mf : fr;
+                vI[jj] = fi > halfm ? fi - mf : fi;
             }
         }
-        const float mf = mc.fm[k], halfm = mc.fhalf[k];
         float v[EPT];
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
-            uint32_t r = p == 0 ? rR[jj] : (p == 1 ? rI[jj] : rR[jj] + rI[jj]);
-            r = r >= m ? r - m : r;
-            float f = __uint_as_float(0x4B000000u | r) - 8388608.0f;
-            v[jj] = f > halfm ? f - mf : f;
+            if (p == 0) v[jj] = vR[jj];
+            else if (p == 1) v[jj] = vI[jj];
+            else {  // Karatsuba operand x_R + x_I, rebalanced
+                float t = vR[jj] + vI[jj];
+                v[jj] = __fmaf_rn(-mf, rint_small(t * imf), t);
+            }
         }
         uint32_t wd[3][WPP];
         const int kind = fp8_kind(k);
@@ -468,7 +493,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             digits_to_words<KIND_B9, EPT>(v, 0.f, wd);
         else
             digits_to_words<KIND_B11, EPT>(v, 0.f, wd);
-        const uint32_t ta = tmem + lanebase + APL_BASE + (uint32_t)(i & 1) * APL_COLS + (uint32_t)(qd * WPP);
+        const uint32_t ta = tmem + lanebase + APL_BASE + (uint32_t)(i % 3) * APL_COLS + (uint32_t)(qd * WPP);
         const int nd = fp8_ndig(k);
 #pragma unroll
         for (int d = 0; d < 3; d++) {
@@ -480,23 +505,24 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             }
         }
     };
-    // MMAs of step i (thread 0 only)
+    // MMAs of step i (thread 0 only).  Constant planes of modulus k live in B
+    // buffer k & 1; B(k+1) is prefetched when step (k, 1) is issued, by which
+    // time every MMA of modulus k-1 (the previous user of that buffer) is done.
     auto issue = [&](int i) -> bool {
         const int k = i / 3, p = i % 3;
         if (p == 0) {
             if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
-            if (k + 1 < NMOD) {  // buffer (k+1)&1 was last read by modulus k-1, whose MMAs are done
-                const uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
-                mbar_expect_tx(smem_u32(&mbar[(k + 1) & 1]), bytes);
-                tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * 9 * planeB),
-                             gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes,
-                             smem_u32(&mbar[(k + 1) & 1]));
-            }
+        }
+        if (p == 1 && k + 1 < NMOD) {
+            const uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
+            mbar_expect_tx(smem_u32(&mbar[(k + 1) & 1]), bytes);
+            tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * 9 * planeB),
+                         gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes, smem_u32(&mbar[(k + 1) & 1]));
         }
         const uint32_t idesc = instr_desc(128, NPAD, 0);
         const uint32_t sBp = smem_u32(sB0 + (k & 1) * 9 * planeB) + (uint32_t)(p * fp8_ndig(k)) * planeB;
         const uint32_t dacc = tmem + (uint32_t)(i & 1) * ACC_COLS;
-        const uint32_t apl = tmem + APL_BASE + (uint32_t)(i & 1) * APL_COLS;
+        const uint32_t apl = tmem + APL_BASE + (uint32_t)(i % 3) * APL_COLS;
         const int kind = fp8_kind(k);
         if (kind == KIND_SQ)
             issue_products_ta<KIND_SQ>(dacc, apl, sBp, NPAD, idesc);
@@ -504,25 +530,26 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             issue_products_ta<KIND_B9>(dacc, apl, sBp, NPAD, idesc);
         else
             issue_products_ta<KIND_B11>(dacc, apl, sBp, NPAD, idesc);
-        tc_commit(smem_u32(&mbar[2]));
+        tc_commit(smem_u32(&mbar[2 + (i & 1)]));
         return true;
     };
 
     gen(0);
+    gen(1);
     tmem_wait_st();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
         tc_fence_after();
-        if (!issue(0)) abort_flag = 1;
+        if (!issue(0) || !issue(1)) abort_flag = 1;
     }
     __syncthreads();
     bool ok = abort_flag == 0;
-    uint32_t mma_phase = 0;
+    uint32_t mph[2] = {0u, 0u};  // next phase parity of the two MMA barriers
     for (int i = 0; i < NSTEP && ok; i++) {
-        if (i + 1 < NSTEP) gen(i + 1);
-        const bool okm = mbar_wait(smem_u32(&mbar[2]), mma_phase, WAIT_LIMIT);
-        mma_phase ^= 1;
+        if (i + 2 < NSTEP) gen(i + 2);
+        const bool okm = mbar_wait(smem_u32(&mbar[2 + (i & 1)]), mph[i & 1], WAIT_LIMIT);
+        mph[i & 1] ^= 1u;
         tc_fence_after();
         const int k = i / 3, p = i % 3;
         if (okm) {
@@ -543,16 +570,18 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 for (int o = 0; o < OPT; o++) Ep[o] = res[o];
             } else {
                 const float mf = mc.fm[k], imf = mc.finv[k];
+                const uint32_t koff = (uint32_t)(k >> 3) * 128 + (uint32_t)(k & 7) * 2;
+                const uint32_t koffI = (uint32_t)((12 + k) >> 3) * 128 + (uint32_t)((12 + k) & 7) * 2;
 #pragma unroll
                 for (int o = 0; o < OPT; o++) {
                     const int kout = qd * OPT + o;
                     if (kout < Kout) {
                         float Rv = canon(Dp[o] - Ep[o], mf, imf);
                         float Iv = canon(res[o] - Dp[o] - Ep[o], mf, imf);
-                        const uint32_t row = (uint32_t)kout * 128 + c;
+                        const uint32_t rowoff = stage_off((uint32_t)kout * 128 + c, 0);
                         const uint32_t hv = f16x2(Rv, Iv);  // exact: canonical residues < 2048
-                        *reinterpret_cast<uint16_t *>(sStage + stage_off(row, k)) = (uint16_t)(hv & 0xFFFFu);
-                        *reinterpret_cast<uint16_t *>(sStage + stage_off(row, 12 + k)) = (uint16_t)(hv >> 16);
+                        *reinterpret_cast<uint16_t *>(sStage + rowoff + koff) = (uint16_t)(hv & 0xFFFFu);
+                        *reinterpret_cast<uint16_t *>(sStage + rowoff + koffI) = (uint16_t)(hv >> 16);
                     }
                 }
             }
@@ -566,9 +595,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             ok = false;
             break;
         }
-        if (tid == 0 && i + 1 < NSTEP) {
+        if (tid == 0 && i + 2 < NSTEP) {
             tc_fence_after();
-            if (!issue(i + 1)) abort_flag = 1;
+            if (!issue(i + 2)) abort_flag = 1;
         }
         // an abort raised by issue() is seen after the next step's barrier
     }
@@ -576,25 +605,37 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // ---------------- CRT Phase A on FP16 tensor cores, then Kulisch + lift + pack ----
     if (ok) {
         fence_async_smem();
-        __syncthreads();
-        ok = mbar_wait(smem_u32(&mbar[3]), 0, WAIT_LIMIT);
+        const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
+        ok = __syncthreads_or(bad) == 0;  // uniform decision across the CTA
         const uint32_t idescA = instr_desc(128, PA_N, 0);
         const int per_wave = 10;
+        const uint32_t ebias[4] = {mc.kbias[0], mc.kbias[1], mc.kbias[2], mc.kbias[3]};
+        const uint64_t zbias = ((uint64_t)mc.zbias[1] << 32) | mc.zbias[0];
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
             const int nb = min(per_wave, Kout - b0);
+            // accumulators start at 2^23: the FP32 bit pattern of 2^23 + P is 0x4B000000 + P
+            for (int bi = qd; bi < nb; bi += 4) {
+                const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
+                tmem_st16_const(ta, 0x4B000000u);
+                tmem_st16_const(ta + 16, 0x4B000000u);
+                tmem_st16_const(ta + 32, 0x4B000000u);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
                 for (int bi = 0; bi < nb; bi++) {
                     uint32_t aaddr = smem_u32(sStage) + (uint32_t)(b0 + bi) * 16 * PA_ROWB;
                     uint32_t d = tmem + (uint32_t)(bi * PA_N);
-                    tc_mma_f16(d, smem_desc(aaddr, 128, PA_ROWB), smem_desc(smem_u32(sPAB), 128, 512), idescA, 0);
+                    tc_mma_f16(d, smem_desc(aaddr, 128, PA_ROWB), smem_desc(smem_u32(sPAB), 128, 512), idescA, 1);
                     tc_mma_f16(d, smem_desc(aaddr + 256, 128, PA_ROWB), smem_desc(smem_u32(sPAB) + 256, 128, 512),
                                idescA, 1);
                 }
                 tc_commit(smem_u32(&mbar[2]));
             }
-            bool okm = mbar_wait(smem_u32(&mbar[2]), mma_phase, WAIT_LIMIT);
-            mma_phase ^= 1;
+            bool okm = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+            mph[0] ^= 1u;
             tc_fence_after();
             if (okm) {
                 for (int bi = qd; bi < nb; bi += 4) {
@@ -612,28 +653,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                         words[16 + i] = r1[i];
                         words[32 + i] = r2[i];
                     }
-                    double res[2];
-#pragma unroll
-                    for (int part = 0; part < 2; part++) {
-                        const uint32_t *wv = words + 24 * part;
-                        uint64_t acc[4] = {0, 0, 0, 0};
-#pragma unroll
-                        for (int s = 0; s < S_RAW; s++) {
-                            uint32_t P = __float_as_uint(__uint_as_float(wv[s]) + 8388608.0f) & 0x7FFFFFu;
-                            acc[s >> 2] += (uint64_t)P << (8 * (s & 3));
-                        }
-                        u128 E = (u128)acc[0] + ((u128)acc[1] << 32) + ((u128)acc[2] << 64) + ((u128)acc[3] << 96);
-                        uint64_t zacc = 0;
-#pragma unroll
-                        for (int t = 0; t < S_FRAC; t++) {
-                            uint32_t Q = __float_as_uint(__uint_as_float(wv[15 + t]) + 8388608.0f) & 0x7FFFFFu;
-                            zacc += (uint64_t)Q << (8 * t);
-                        }
-                        int64_t zhat = (int64_t)((zacc + (1ull << 47)) >> 48);
-                        i128 R = lift_two_sided(E, zhat, mc);
-                        res[part] = pack_rne(R, e - 104);
-                    }
-                    if (cvalid && kout < Kout) out[map.out_index(cg, kout)] = make_double2(res[0], res[1]);
+                    const double re = kulisch_pack_fp8(words, mc, e - 104, ebias, zbias);
+                    const double im = kulisch_pack_fp8(words + 24, mc, e - 104, ebias, zbias);
+                    if (cvalid && kout < Kout) out[obase + (int64_t)kout * ostride] = make_double2(re, im);
                 }
             } else {
                 atomicExch(&abort_flag, 1);
@@ -645,7 +667,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     }
     if (!ok && tid == 0) {
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
-        mbar_wait(smem_u32(&mbar[2]), mma_phase, WAIT_LIMIT);  // let in-flight MMAs drain (bounded)
+        // let in-flight MMAs drain (bounded) before the TMEM is freed
+        mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+        mbar_wait(smem_u32(&mbar[3]), mph[1], WAIT_LIMIT);
     }
     tc_fence_before();
     __syncthreads();

@@ -133,6 +133,12 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t a, uint32_t b)
 __device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t a) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(a) : "memory");
 }
+__device__ __forceinline__ void tmem_st16_const(uint32_t taddr, uint32_t v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(v)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -157,6 +163,10 @@ __device__ __forceinline__ uint32_t f16x2(float lo, float hi) {
 // round-to-nearest-even integer of |x| < 2^22 in FP32 (magic-number add)
 __device__ __forceinline__ float rint_small(float x) {
     return __fadd_rn(__fadd_rn(x, 12582912.0f), -12582912.0f);
+}
+// RNE integer of a * b + c for |a b + c| < 2^22 (fused, one rounding before the magic add)
+__device__ __forceinline__ float rint_fma(float a, float b, float c) {
+    return __fadd_rn(__fmaf_rn(a, b, c + 12582912.0f), -12582912.0f);
 }
 
 }  // namespace obfft

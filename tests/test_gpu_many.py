@@ -1,0 +1,74 @@
+"""A10: several grids of uneven sizes in one plan, executed as one captured
+CUDA graph; results bit-identical to single-grid plans and to the oracle, the
+graph replayed on later calls, and the split autotuner's choice honoured."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+from synth import inputs as S
+from tests.helpers import bits_equal, mismatch_report, oracle_full
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(16, 16, 16), (8, 12, 24), (16, 16, 16), (32, 8, 16), (4, 4, 96)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2606_23698_gb300 import build as B
+    B.build()
+
+
+@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64"])
+def test_many_matches_single_plans_and_replays(mode):
+    from paper_2606_23698_gb300 import Plan, PlanMany
+    xs = [S.complex_gaussian(S.SEED_UNEVEN + i, d).to("cuda") for i, d in enumerate(DIMS)]
+    pm = PlanMany(DIMS, mode=mode)
+    outs = [torch.empty_like(x) for x in xs]
+    for rep in range(3):  # first call captures, later calls replay the graph
+        pm.exec(xs, outs, dir=-1)
+        torch.cuda.synchronize()
+        for d, x, o in zip(DIMS, xs, outs):
+            ref = Plan(*d, batch=1, mode=mode).exec(x, dir=-1)
+            torch.cuda.synchronize()
+            assert bits_equal(o.cpu().numpy(), ref.cpu().numpy()), (mode, d, rep)
+    # new pointers: recapture
+    outs2 = [torch.empty_like(x) for x in xs]
+    pm.exec(xs, outs2, dir=+1)
+    torch.cuda.synchronize()
+    if mode != "fp64":
+        for i, d in enumerate(DIMS[:3]):
+            sp = tuple(pm_split(pm, i, a) for a in range(3))
+            want = oracle_full(xs[i].cpu().numpy(), sp, +1)
+            got = outs2[i].cpu().numpy()
+            assert bits_equal(got, want), mismatch_report(got, want)
+
+
+def pm_split(pm, grid, axis):
+    from paper_2606_23698_gb300 import _lib
+    return _lib.obfft_plan_get_splits(pm.handle, grid, axis)
+
+
+def test_autotuned_splits_stay_exact():
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+from paper_2606_23698_gb300 import Plan
+from synth import inputs as S
+from tests.helpers import oracle_full, bits_equal
+shape = (8, 96, 48)
+x = S.complex_uniform(7, shape).numpy()
+pl = Plan(*shape, mode="fp8")
+sp = tuple(pl.splits(a) for a in range(3))
+y = pl.exec(torch.from_numpy(x).cuda()).cpu().numpy()
+assert bits_equal(y, oracle_full(x, sp, -1)), sp
+print("splits", sp)
+''' % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, OBFFT_AUTOTUNE="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "splits" in r.stdout
