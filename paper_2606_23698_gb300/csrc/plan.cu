@@ -306,7 +306,8 @@ std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups,
                 for (int n = 0; n < K; n++)
                     for (int j = 0; j < K; j++) {
                         const int64_t *e = &F[(((size_t)g * K + n) * K + j) * 2];
-                        int64_t a = p == 0 ? e[0] : p == 1 ? e[1] : e[0] + e[1];
+                        // constant planes of the complex product in real form: a_R, a_I, -a_I
+                        int64_t a = p == 0 ? e[0] : p == 1 ? e[1] : -e[1];
                         int64_t r = modc(a, m);
                         int64_t v = 2 * r > m ? r - m : r;  // balanced
                         int dig[3];

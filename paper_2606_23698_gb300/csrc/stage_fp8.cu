@@ -1,25 +1,32 @@
 // FP8-mode Bailey stage on Blackwell tensor cores (tcgen05, sm_103a).
 //
 // One CTA transforms 128 columns (one Ozaki-II complex GEMM per column,
-// Algorithm 1, one half).  Per modulus m_k and Karatsuba product
-// (D = A_R B_R, E = A_I B_I, F = (A_R + A_I)(B_R + B_I), Background):
-//   * the data residues (canonical x~ mod m_k, then balanced) are split into
-//     E4M3-exact digit planes by the SIMT threads and stored to shared memory
-//     in the UMMA K-major layout (row = column of the DFT, 32 bytes of K);
-//   * the constant DFT / twiddle-fused matrix digits arrive by TMA bulk copy;
-//   * tcgen05.mma kind::f8f6f4 (M = 128, N = 16/32, K = 32) accumulates each
-//     weight class of digit products in TMEM (FP32, every partial sum an
-//     integer far below 2^24: exact);
+// Algorithm 1, one half).  Per modulus m_k:
+//   * the data residues (canonical x~ mod m_k, then balanced) of the real and
+//     imaginary parts are split into E4M3-exact digit planes by the SIMT
+//     threads and written straight into tensor memory, where tcgen05.mma reads
+//     them as its A operand (row = column of the DFT, 32 bytes of K);
+//   * the constant DFT / twiddle-fused matrix digits (planes of a_R, a_I and
+//     -a_I) arrive in shared memory by TMA bulk copy, double buffered;
+//   * the complex product is formed in real form, Re = a_R b_R + (-a_I) b_I and
+//     Im = a_I b_R + a_R b_I, as two pipelined steps per modulus: tcgen05.mma
+//     kind::f8f6f4 (M = 128, N = 16/32, K = 32) accumulates each weight class of
+//     digit products in TMEM (FP32, every partial sum an integer below 2^17:
+//     exact).  On this GPU the tensor pipe has ample headroom and the SIMT
+//     epilogue is the bottleneck, so the fourth real product is cheaper than the
+//     Karatsuba operand a_R + a_I and the residue-domain combine it would need
+//     (the INT8 mode keeps the paper's Karatsuba split);
 //   * the epilogue reads the classes back (tcgen05.ld), recombines them with
-//     their weights, reduces mod m_k, forms R_k = D - E and I_k = F - D - E,
-//     canonicalises to [0, m_k) and writes the FP16 CRT operand
-//     (Sec. tcgarner: residues < 2048 are FP16-exact) to shared memory.
+//     their weights, reduces mod m_k to the canonical residue and writes the
+//     FP16 CRT operand (Sec. tcgarner: residues < 2048 are FP16-exact) to
+//     shared memory.
 // After the 12 moduli, CRT Phase A runs as tcgen05.mma kind::f16 (M = 128
 // complex outputs, N = 48 = Re/Im x (15 byte slices of u_k + 6 of w_k + 3
-// pad), K = 24 = Re/Im x 12 moduli, FP32 accumulation exact below 2^24,
-// Eq. phaseAcost), and each thread finishes its outputs with the Kulisch
-// sum E = sum_s P_s 256^s, the lift quotient from the w_k columns, the
-// two-sided modulo-M correction and the correctly rounded pack (Algorithm 2).
+// pad), K = 24 = Re/Im x 12 moduli, accumulators preset to 2^23, FP32
+// accumulation exact below 2^24, Eq. phaseAcost), and each thread finishes its
+// outputs with the Kulisch sum E = sum_s P_s 256^s, the lift quotient from the
+// w_k columns, the two-sided modulo-M correction and the correctly rounded
+// pack (Algorithm 2).
 //
 // Digit layouts (exhaustively verified on the host, see the FP8 layout tests):
 //   m = s^2 (1089, 1024, 961, 841, 625, 529): v = s h + l, |h|, |l| <= 16;
@@ -241,12 +248,13 @@ __device__ __forceinline__ float canon(float x, float m, float im) {
 // pipelined: the digits of step i+1 are generated (into the other TMEM
 // A-buffer) while the MMAs of step i run; TMEM accumulators and the TMA-loaded
 // constant planes are double buffered.
-// TMEM columns: accumulators [0,160) and [160,320), A digit planes in three
-// buffers [320,344), [344,368), [368,392); Phase A reuses [0,480).  Two MMA
-// steps are in flight while a third step's digits are generated.
+// TMEM columns: accumulators [0,160) and [160,320); A digit planes of x_R
+// (planes 0..2) and x_I (planes 3..5) of one modulus in two buffers [320,368)
+// and [368,416); Phase A reuses [0,480).  Two MMA steps are in flight while the
+// next modulus' digits are generated.
 // ---------------------------------------------------------------------------
 constexpr int FP8_WARPS = 16;
-constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 24, N_ABUF = 3;
+constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 48, N_ABUF = 2;
 
 template <int NPAD>
 struct Fp8Cfg {
@@ -294,33 +302,44 @@ __device__ __forceinline__ void digits_to_words(const float (&v)[EPT], float s, 
     }
 }
 
+// Digit-pair MMAs of one (modulus, part) step of the complex product in real
+// form: Re = sum a_R b_R + (-a_I) b_I, Im = sum a_I b_R + a_R b_I.  Constant
+// planes per modulus: [a_R digits][a_I digits][-a_I digits]; data planes in the
+// A buffer: [b_R digits (planes 0..2)][b_I digits (planes 3..5)].  Each weight
+// class of digit pairs accumulates in one TMEM accumulator (K = 2 x 32 terms).
 template <int KIND>
-__device__ __forceinline__ void issue_products_ta(uint32_t dacc, uint32_t apl, uint32_t sBp, int npad,
-                                                  uint32_t idesc) {
+__device__ __forceinline__ void issue_part_ta(uint32_t dacc, uint32_t apl, uint32_t sBm, int npad, int part,
+                                              uint32_t idesc) {
+    constexpr int ND = KIND == KIND_B11 ? 3 : 2;
     const uint32_t planeB = (uint32_t)npad * 32;
-    auto mma = [&](int ci, int dj, int cls, uint32_t acc) {
-        uint64_t b = smem_desc(sBp + ci * planeB, 128, 256);
-        tc_mma_f8_ta(dacc + cls * npad, apl + dj * 8, b, idesc, acc);
+    // constant operand for the x_R half and the x_I half of this part
+    const int cR = part == 0 ? 0 : 1;  // a_R (Re) or a_I (Im)
+    const int cI = part == 0 ? 2 : 0;  // -a_I (Re) or a_R (Im)
+    auto mma2 = [&](int ci, int dj, int cls, uint32_t first) {
+        tc_mma_f8_ta(dacc + cls * npad, apl + dj * 8, smem_desc(sBm + (cR * ND + ci) * planeB, 128, 256), idesc,
+                     first ? 0u : 1u);
+        tc_mma_f8_ta(dacc + cls * npad, apl + (3 + dj) * 8, smem_desc(sBm + (cI * ND + ci) * planeB, 128, 256),
+                     idesc, 1u);
     };
     if (KIND == KIND_SQ) {  // digits 0 = h, 1 = l
-        mma(0, 1, 1, 0);
-        mma(1, 0, 1, 1);
-        mma(1, 1, 0, 0);
+        mma2(0, 1, 1, 1);
+        mma2(1, 0, 1, 0);
+        mma2(1, 1, 0, 1);
     } else if (KIND == KIND_B9) {
-        mma(0, 0, 0, 0);
-        mma(0, 1, 1, 0);
-        mma(1, 0, 1, 1);
-        mma(1, 1, 2, 0);
+        mma2(0, 0, 0, 1);
+        mma2(0, 1, 1, 1);
+        mma2(1, 0, 1, 0);
+        mma2(1, 1, 2, 1);
     } else {
-        mma(0, 0, 0, 0);
-        mma(0, 1, 1, 0);
-        mma(1, 0, 1, 1);
-        mma(0, 2, 2, 0);
-        mma(1, 1, 2, 1);
-        mma(2, 0, 2, 1);
-        mma(1, 2, 3, 0);
-        mma(2, 1, 3, 1);
-        mma(2, 2, 4, 0);
+        mma2(0, 0, 0, 1);
+        mma2(0, 1, 1, 1);
+        mma2(1, 0, 1, 0);
+        mma2(0, 2, 2, 1);
+        mma2(1, 1, 2, 0);
+        mma2(2, 0, 2, 0);
+        mma2(1, 2, 3, 1);
+        mma2(2, 1, 3, 0);
+        mma2(2, 2, 4, 1);
     }
 }
 
@@ -373,7 +392,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                      const double2 *__restrict__ in, double2 *__restrict__ out, int *status) {
     using CF = Fp8Cfg<NPAD>;
     constexpr int EPT = CF::EPT, OPT = CF::OPT, WPP = CF::WPP;
-    constexpr int NSTEP = 3 * NMOD;
+    constexpr int NSTEP = 2 * NMOD;  // (modulus, Re / Im) steps
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ ModConsts mc;
     __shared__ int colpart[4][128];
@@ -418,12 +437,12 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
         tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
     }
-    // K <= 16: bytes 16..31 of every A row stay zero (columns 4..7 of each plane)
+    // K <= 16: bytes 16..31 of every A row stay zero (columns 4..7 of each of the 6 planes)
     if (NPAD == 16 && qd == 0) {
 #pragma unroll
         for (int b = 0; b < (int)N_ABUF; b++)
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
+            for (int d = 0; d < 6; d++) {
                 uint32_t ta = tmem + lanebase + APL_BASE + b * APL_COLS + d * 8 + 4;
                 tmem_st2(ta, 0u, 0u);
                 tmem_st2(ta + 2, 0u, 0u);
@@ -458,84 +477,75 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         }
     }
 
-    float vR[EPT], vI[EPT];
-    float Dp[OPT], Ep[OPT];
-    // digits of step i into A buffer (i % 3)
-    auto gen = [&](int i) {
-        const int k = i / 3, p = i % 3;
-        const float mf = mc.fm[k], imf = mc.finv[k];
-        if (p == 0) {  // balanced residues of x~_R and x~_I for modulus k
-            const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
-            const float halfm = mc.fhalf[k];
-#pragma unroll
-            for (int jj = 0; jj < EPT; jj++) {
-                float fr = __uint_as_float(0x4B000000u | residue(pR[jj], m, mu, c20, c40, cn)) - 8388608.0f;
-                float fi = __uint_as_float(0x4B000000u | residue(pI[jj], m, mu, c20, c40, cn)) - 8388608.0f;
-                vR[jj] = fr > halfm ? fr - mf : fr;
-                vI[jj] = fi > halfm ? fi - mf : fi;
-            }
-        }
-        float v[EPT];
+    // digits of x_R and x_I for modulus k into A buffer (k & 1)
+    auto gen = [&](int k) {
+        const float mf = mc.fm[k];
+        const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
+        const float halfm = mc.fhalf[k];
+        float vR[EPT], vI[EPT];
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
-            if (p == 0) v[jj] = vR[jj];
-            else if (p == 1) v[jj] = vI[jj];
-            else {  // Karatsuba operand x_R + x_I, rebalanced
-                float t = vR[jj] + vI[jj];
-                v[jj] = __fmaf_rn(-mf, rint_small(t * imf), t);
-            }
+            float fr = __uint_as_float(0x4B000000u | residue(pR[jj], m, mu, c20, c40, cn)) - 8388608.0f;
+            float fi = __uint_as_float(0x4B000000u | residue(pI[jj], m, mu, c20, c40, cn)) - 8388608.0f;
+            vR[jj] = fr > halfm ? fr - mf : fr;  // balanced
+            vI[jj] = fi > halfm ? fi - mf : fi;
         }
-        uint32_t wd[3][WPP];
+        uint32_t wR[3][WPP], wI[3][WPP];
         const int kind = fp8_kind(k);
-        if (kind == KIND_SQ)
-            digits_to_words<KIND_SQ, EPT>(v, mc.fsq[k], wd);
-        else if (kind == KIND_B9)
-            digits_to_words<KIND_B9, EPT>(v, 0.f, wd);
-        else
-            digits_to_words<KIND_B11, EPT>(v, 0.f, wd);
-        const uint32_t ta = tmem + lanebase + APL_BASE + (uint32_t)(i % 3) * APL_COLS + (uint32_t)(qd * WPP);
+        if (kind == KIND_SQ) {
+            digits_to_words<KIND_SQ, EPT>(vR, mc.fsq[k], wR);
+            digits_to_words<KIND_SQ, EPT>(vI, mc.fsq[k], wI);
+        } else if (kind == KIND_B9) {
+            digits_to_words<KIND_B9, EPT>(vR, 0.f, wR);
+            digits_to_words<KIND_B9, EPT>(vI, 0.f, wI);
+        } else {
+            digits_to_words<KIND_B11, EPT>(vR, 0.f, wR);
+            digits_to_words<KIND_B11, EPT>(vI, 0.f, wI);
+        }
+        const uint32_t ta = tmem + lanebase + APL_BASE + (uint32_t)(k & 1) * APL_COLS + (uint32_t)(qd * WPP);
         const int nd = fp8_ndig(k);
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             if (d < nd) {
-                if constexpr (WPP == 2)
-                    tmem_st2(ta + d * 8, wd[d][0], wd[d][1]);
-                else
-                    tmem_st1(ta + d * 8, wd[d][0]);
+                if constexpr (WPP == 2) {
+                    tmem_st2(ta + d * 8, wR[d][0], wR[d][1]);
+                    tmem_st2(ta + (3 + d) * 8, wI[d][0], wI[d][1]);
+                } else {
+                    tmem_st1(ta + d * 8, wR[d][0]);
+                    tmem_st1(ta + (3 + d) * 8, wI[d][0]);
+                }
             }
         }
     };
-    // MMAs of step i (thread 0 only).  Constant planes of modulus k live in B
-    // buffer k & 1; B(k+1) is prefetched when step (k, 1) is issued, by which
-    // time every MMA of modulus k-1 (the previous user of that buffer) is done.
+    // MMAs of step i = (modulus k, part) (thread 0 only).  Constant planes of
+    // modulus k live in B buffer k & 1; B(k+1) is prefetched when step (k, Im)
+    // is issued, by which time every MMA of modulus k-1 is done.
     auto issue = [&](int i) -> bool {
-        const int k = i / 3, p = i % 3;
-        if (p == 0) {
+        const int k = i >> 1, part = i & 1;
+        if (part == 0) {
             if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
-        }
-        if (p == 1 && k + 1 < NMOD) {
+        } else if (k + 1 < NMOD) {
             const uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
             mbar_expect_tx(smem_u32(&mbar[(k + 1) & 1]), bytes);
             tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * 9 * planeB),
                          gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes, smem_u32(&mbar[(k + 1) & 1]));
         }
         const uint32_t idesc = instr_desc(128, NPAD, 0);
-        const uint32_t sBp = smem_u32(sB0 + (k & 1) * 9 * planeB) + (uint32_t)(p * fp8_ndig(k)) * planeB;
+        const uint32_t sBm = smem_u32(sB0 + (k & 1) * 9 * planeB);
         const uint32_t dacc = tmem + (uint32_t)(i & 1) * ACC_COLS;
-        const uint32_t apl = tmem + APL_BASE + (uint32_t)(i % 3) * APL_COLS;
+        const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * APL_COLS;
         const int kind = fp8_kind(k);
         if (kind == KIND_SQ)
-            issue_products_ta<KIND_SQ>(dacc, apl, sBp, NPAD, idesc);
+            issue_part_ta<KIND_SQ>(dacc, apl, sBm, NPAD, part, idesc);
         else if (kind == KIND_B9)
-            issue_products_ta<KIND_B9>(dacc, apl, sBp, NPAD, idesc);
+            issue_part_ta<KIND_B9>(dacc, apl, sBm, NPAD, part, idesc);
         else
-            issue_products_ta<KIND_B11>(dacc, apl, sBp, NPAD, idesc);
+            issue_part_ta<KIND_B11>(dacc, apl, sBm, NPAD, part, idesc);
         tc_commit(smem_u32(&mbar[2 + (i & 1)]));
         return true;
     };
 
     gen(0);
-    gen(1);
     tmem_wait_st();
     tc_fence_before();
     __syncthreads();
@@ -547,11 +557,12 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     bool ok = abort_flag == 0;
     uint32_t mph[2] = {0u, 0u};  // next phase parity of the two MMA barriers
     for (int i = 0; i < NSTEP && ok; i++) {
-        if (i + 2 < NSTEP) gen(i + 2);
+        // digits of modulus k+1 while the two steps of modulus k run
+        if ((i & 1) == 0 && (i >> 1) + 1 < NMOD) gen((i >> 1) + 1);
         const bool okm = mbar_wait(smem_u32(&mbar[2 + (i & 1)]), mph[i & 1], WAIT_LIMIT);
         mph[i & 1] ^= 1u;
         tc_fence_after();
-        const int k = i / 3, p = i % 3;
+        const int k = i >> 1, part = i & 1;
         if (okm) {
             float res[OPT];
             const uint32_t tacc = tmem + lanebase + (uint32_t)(i & 1) * ACC_COLS + (uint32_t)(qd * OPT);
@@ -562,28 +573,24 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 read_classes<KIND_B9, OPT>(tacc, NPAD, mc, k, res);
             else
                 read_classes<KIND_B11, OPT>(tacc, NPAD, mc, k, res);
-            if (p == 0) {
+            const float mf = mc.fm[k], imf = mc.finv[k];
+            const int kk = part == 0 ? k : 12 + k;  // staging column: Re residues, then Im
+            const uint32_t koff = (uint32_t)(kk >> 3) * 128 + (uint32_t)(kk & 7) * 2;
+            float cv[OPT];
+            // res is congruent and within +-1.5 m (the FP32 quotient may miss by one
+            // near a half-integer); canon() returns the canonical residue in [0, m)
 #pragma unroll
-                for (int o = 0; o < OPT; o++) Dp[o] = res[o];
-            } else if (p == 1) {
+            for (int o = 0; o < OPT; o++) cv[o] = canon(res[o], mf, imf);
 #pragma unroll
-                for (int o = 0; o < OPT; o++) Ep[o] = res[o];
-            } else {
-                const float mf = mc.fm[k], imf = mc.finv[k];
-                const uint32_t koff = (uint32_t)(k >> 3) * 128 + (uint32_t)(k & 7) * 2;
-                const uint32_t koffI = (uint32_t)((12 + k) >> 3) * 128 + (uint32_t)((12 + k) & 7) * 2;
-#pragma unroll
-                for (int o = 0; o < OPT; o++) {
-                    const int kout = qd * OPT + o;
-                    if (kout < Kout) {
-                        float Rv = canon(Dp[o] - Ep[o], mf, imf);
-                        float Iv = canon(res[o] - Dp[o] - Ep[o], mf, imf);
-                        const uint32_t rowoff = stage_off((uint32_t)kout * 128 + c, 0);
-                        const uint32_t hv = f16x2(Rv, Iv);  // exact: canonical residues < 2048
-                        *reinterpret_cast<uint16_t *>(sStage + rowoff + koff) = (uint16_t)(hv & 0xFFFFu);
-                        *reinterpret_cast<uint16_t *>(sStage + rowoff + koffI) = (uint16_t)(hv >> 16);
-                    }
-                }
+            for (int o = 0; o + 1 < OPT; o += 2) {
+                const uint32_t hv = f16x2(cv[o], cv[o + 1]);  // exact: canonical residues < 2048
+                const int k0 = qd * OPT + o;
+                if (k0 < Kout)
+                    *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)k0 * 128 + c, 0) + koff) =
+                        (uint16_t)(hv & 0xFFFFu);
+                if (k0 + 1 < Kout)
+                    *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)(k0 + 1) * 128 + c, 0) + koff) =
+                        (uint16_t)(hv >> 16);
             }
         } else {
             atomicExch(&abort_flag, 1);

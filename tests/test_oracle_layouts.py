@@ -13,6 +13,13 @@ def test_fp8_layout_exact(m):
 
 
 @pytest.mark.parametrize("m", C.MODULI)
+def test_fp8_layout_exact_for_real_form_complex_product(m):
+    """Re = a_R b_R + (-a_I) b_I accumulates 2 x 32 digit products per class."""
+    info = LY.check_fp8_layout(m, K=64)
+    assert info["max_combined"] < 2 ** 24
+
+
+@pytest.mark.parametrize("m", C.MODULI)
 def test_int8_two_limb(m):
     LY.check_int8_two_limb(m)
 
