@@ -235,7 +235,10 @@ __device__ __forceinline__ void read_product(uint32_t tlane, int npad, int hf, c
 
 // canonical residue in [0, m) of an exact small integer x (|x| < 2^20), FP32
 __device__ __forceinline__ float canon(float x, float m, float im) {
-    float r = __fmaf_rn(-m, floorf(x * im), x);
+    // q = rint(x / m) up to one unit near half-integers (FP32 quotient), so
+    // r = x - m q lies in (-m, m); the fix-ups map it to [0, m)
+    float q = rint_fma(x, im, 0.f);
+    float r = __fmaf_rn(-m, q, x);
     r = r < 0.f ? r + m : r;
     return r >= m ? r - m : r;
 }
@@ -276,19 +279,19 @@ __device__ __forceinline__ void digits_to_words(const float (&v)[EPT], float s, 
             for (int e2 = 0; e2 < 2; e2++) {
                 float x = v[q4 * 4 + h2 * 2 + e2];
                 if constexpr (KIND == KIND_SQ) {
-                    float h = rint_small(x * (1.0f / s));
+                    float h = rint_fma(x, 1.0f / s, 0.f);
                     dg[0][e2] = h;
                     dg[1][e2] = __fmaf_rn(-s, h, x);
                     dg[2][e2] = 0.f;
                 } else if constexpr (KIND == KIND_B9) {
-                    float d1 = rint_small(x * 0.0625f);
+                    float d1 = rint_fma(x, 0.0625f, 0.f);
                     dg[1][e2] = d1;
                     dg[0][e2] = __fmaf_rn(-16.0f, d1, x);
                     dg[2][e2] = 0.f;
                 } else {
-                    float d2 = rint_small(x * 0.00390625f);
+                    float d2 = rint_fma(x, 0.00390625f, 0.f);
                     float r = __fmaf_rn(-256.0f, d2, x);
-                    float d1 = rint_small(r * 0.0625f);
+                    float d1 = rint_fma(r, 0.0625f, 0.f);
                     dg[2][e2] = d2;
                     dg[1][e2] = d1;
                     dg[0][e2] = __fmaf_rn(-16.0f, d1, r);
@@ -343,7 +346,7 @@ __device__ __forceinline__ void issue_part_ta(uint32_t dacc, uint32_t apl, uint3
     }
 }
 
-// class accumulators of this thread's OPT outputs -> balanced residue mod m
+// class accumulators of this thread's OPT outputs -> their weighted sum (exact)
 template <int KIND, int OPT>
 __device__ __forceinline__ void read_classes(uint32_t tacc, int npad, const ModConsts &mc, int k,
                                              float (&out)[OPT]) {
@@ -375,13 +378,12 @@ __device__ __forceinline__ void read_classes(uint32_t tacc, int npad, const ModC
         wts[3] = mc.fc3[k];
         wts[4] = mc.fc4[k];
     }
-    const float m = mc.fm[k], im = mc.finv[k];
 #pragma unroll
     for (int i = 0; i < OPT; i++) {
         float a = __uint_as_float(r[0][i]);
 #pragma unroll
         for (int cl = 1; cl < NC; cl++) a = __fmaf_rn(wts[cl], __uint_as_float(r[cl][i]), a);
-        out[i] = __fmaf_rn(-m, rint_small(a * im), a);
+        out[i] = a;  // exact integer, |a| < 2^24, congruent to sum_j a_j b_j mod m
     }
 }
 
@@ -577,8 +579,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             const int kk = part == 0 ? k : 12 + k;  // staging column: Re residues, then Im
             const uint32_t koff = (uint32_t)(kk >> 3) * 128 + (uint32_t)(kk & 7) * 2;
             float cv[OPT];
-            // res is congruent and within +-1.5 m (the FP32 quotient may miss by one
-            // near a half-integer); canon() returns the canonical residue in [0, m)
+            // canonical residue in [0, m) of the exact class sum (|res| < 2^24: the FP32
+            // quotient is within one of the true one, canon() fixes either side)
 #pragma unroll
             for (int o = 0; o < OPT; o++) cv[o] = canon(res[o], mf, imf);
 #pragma unroll
