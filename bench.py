@@ -232,6 +232,16 @@ def side_configs(torch, Plan, PlanMany, S, mode):
     return out
 
 
+def max_over_ranks(dist, value: float, device="cpu") -> float:
+    """Whole-job time of N replicas: the slowest rank's time (all_reduce MAX)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------- our arm ----
 def main():
     args = parse()
@@ -279,11 +289,7 @@ def main():
             pl.exec(x, y)
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device="cuda")
         return pl, ms
 
     # headline mode, timed with clock sampling
