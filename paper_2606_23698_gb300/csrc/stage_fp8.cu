@@ -251,10 +251,10 @@ __device__ __forceinline__ float canon(float x, float m, float im) {
 // pipelined: the digits of step i+1 are generated (into the other TMEM
 // A-buffer) while the MMAs of step i run; TMEM accumulators and the TMA-loaded
 // constant planes are double buffered.
-// TMEM columns: accumulators [0,160) and [160,320); A digit planes of x_R
-// (planes 0..2) and x_I (planes 3..5) of one modulus in two buffers [320,368)
-// and [368,416); Phase A reuses [0,480).  Two MMA steps are in flight while the
-// next modulus' digits are generated.
+// TMEM columns: class accumulators of Re [0,160) and Im [160,320); A digit
+// planes of x_R (planes 0..2) and x_I (planes 3..5) of one modulus in two
+// buffers [320,368) and [368,416); Phase A reuses [0,480).  One pipeline step
+// per modulus: its MMAs run while the next modulus' digits are generated.
 // ---------------------------------------------------------------------------
 constexpr int FP8_WARPS = 16;
 constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 48, N_ABUF = 2;
@@ -311,18 +311,18 @@ __device__ __forceinline__ void digits_to_words(const float (&v)[EPT], float s, 
 // A buffer: [b_R digits (planes 0..2)][b_I digits (planes 3..5)].  Each weight
 // class of digit pairs accumulates in one TMEM accumulator (K = 2 x 32 terms).
 template <int KIND>
-__device__ __forceinline__ void issue_part_ta(uint32_t dacc, uint32_t apl, uint32_t sBm, int npad, int part,
+__device__ __forceinline__ void issue_part_ta(uint32_t dacc, uint32_t apl, uint64_t bdesc, int npad, int part,
                                               uint32_t idesc) {
     constexpr int ND = KIND == KIND_B11 ? 3 : 2;
-    const uint32_t planeB = (uint32_t)npad * 32;
+    const uint32_t planeB16 = (uint32_t)npad * 2;  // plane size in 16-byte descriptor units
     // constant operand for the x_R half and the x_I half of this part
     const int cR = part == 0 ? 0 : 1;  // a_R (Re) or a_I (Im)
     const int cI = part == 0 ? 2 : 0;  // -a_I (Re) or a_R (Im)
     auto mma2 = [&](int ci, int dj, int cls, uint32_t first) {
-        tc_mma_f8_ta(dacc + cls * npad, apl + dj * 8, smem_desc(sBm + (cR * ND + ci) * planeB, 128, 256), idesc,
+        tc_mma_f8_ta(dacc + cls * npad, apl + dj * 8, bdesc + (uint64_t)((cR * ND + ci) * planeB16), idesc,
                      first ? 0u : 1u);
-        tc_mma_f8_ta(dacc + cls * npad, apl + (3 + dj) * 8, smem_desc(sBm + (cI * ND + ci) * planeB, 128, 256),
-                     idesc, 1u);
+        tc_mma_f8_ta(dacc + cls * npad, apl + (3 + dj) * 8, bdesc + (uint64_t)((cI * ND + ci) * planeB16), idesc,
+                     1u);
     };
     if (KIND == KIND_SQ) {  // digits 0 = h, 1 = l
         mma2(0, 1, 1, 1);
@@ -394,11 +394,11 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                      const double2 *__restrict__ in, double2 *__restrict__ out, int *status) {
     using CF = Fp8Cfg<NPAD>;
     constexpr int EPT = CF::EPT, OPT = CF::OPT, WPP = CF::WPP;
-    constexpr int NSTEP = 2 * NMOD;  // (modulus, Re / Im) steps
+    constexpr int NSTEP = NMOD;  // one pipeline step per modulus
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ ModConsts mc;
     __shared__ int colpart[4][128];
-    __shared__ __align__(8) uint64_t mbar[5];  // 0,1: B planes (TMA, per buffer), 2,3: MMA, 4: Phase-A B
+    __shared__ __align__(8) uint64_t mbar[5];  // 0,1: B planes (TMA, per buffer), 2: MMA, 4: Phase-A B
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
@@ -519,31 +519,34 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             }
         }
     };
-    // MMAs of step i = (modulus k, part) (thread 0 only).  Constant planes of
-    // modulus k live in B buffer k & 1; B(k+1) is prefetched when step (k, Im)
-    // is issued, by which time every MMA of modulus k-1 is done.
-    auto issue = [&](int i) -> bool {
-        const int k = i >> 1, part = i & 1;
-        if (part == 0) {
-            if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
-        } else if (k + 1 < NMOD) {
+    // MMAs of modulus k, Re then Im part (thread 0 only).  Constant planes of
+    // modulus k live in B buffer k & 1; B(k+1) is prefetched here, into the
+    // buffer of modulus k-1, whose MMAs have completed.
+    const uint64_t bdesc0 = smem_desc(smem_u32(sB0), 128, 256);
+    const uint64_t bdesc1 = smem_desc(smem_u32(sB0 + 9 * planeB), 128, 256);
+    auto issue = [&](int k) -> bool {
+        if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
+        if (k + 1 < NMOD) {
             const uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
             mbar_expect_tx(smem_u32(&mbar[(k + 1) & 1]), bytes);
             tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * 9 * planeB),
                          gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes, smem_u32(&mbar[(k + 1) & 1]));
         }
         const uint32_t idesc = instr_desc(128, NPAD, 0);
-        const uint32_t sBm = smem_u32(sB0 + (k & 1) * 9 * planeB);
-        const uint32_t dacc = tmem + (uint32_t)(i & 1) * ACC_COLS;
+        const uint64_t bd = (k & 1) ? bdesc1 : bdesc0;
         const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * APL_COLS;
         const int kind = fp8_kind(k);
-        if (kind == KIND_SQ)
-            issue_part_ta<KIND_SQ>(dacc, apl, sBm, NPAD, part, idesc);
-        else if (kind == KIND_B9)
-            issue_part_ta<KIND_B9>(dacc, apl, sBm, NPAD, part, idesc);
-        else
-            issue_part_ta<KIND_B11>(dacc, apl, sBm, NPAD, part, idesc);
-        tc_commit(smem_u32(&mbar[2 + (i & 1)]));
+#pragma unroll
+        for (int part = 0; part < 2; part++) {
+            const uint32_t dacc = tmem + (uint32_t)part * ACC_COLS;
+            if (kind == KIND_SQ)
+                issue_part_ta<KIND_SQ>(dacc, apl, bd, NPAD, part, idesc);
+            else if (kind == KIND_B9)
+                issue_part_ta<KIND_B9>(dacc, apl, bd, NPAD, part, idesc);
+            else
+                issue_part_ta<KIND_B11>(dacc, apl, bd, NPAD, part, idesc);
+        }
+        tc_commit(smem_u32(&mbar[2]));
         return true;
     };
 
@@ -553,46 +556,47 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     __syncthreads();
     if (tid == 0) {
         tc_fence_after();
-        if (!issue(0) || !issue(1)) abort_flag = 1;
+        if (!issue(0)) abort_flag = 1;
     }
     __syncthreads();
     bool ok = abort_flag == 0;
-    uint32_t mph[2] = {0u, 0u};  // next phase parity of the two MMA barriers
-    for (int i = 0; i < NSTEP && ok; i++) {
-        // digits of modulus k+1 while the two steps of modulus k run
-        if ((i & 1) == 0 && (i >> 1) + 1 < NMOD) gen((i >> 1) + 1);
-        const bool okm = mbar_wait(smem_u32(&mbar[2 + (i & 1)]), mph[i & 1], WAIT_LIMIT);
-        mph[i & 1] ^= 1u;
+    uint32_t mph[1] = {0u};  // next phase parity of the MMA barrier mbar[2]
+    for (int k = 0; k < NSTEP && ok; k++) {
+        if (k + 1 < NMOD) gen(k + 1);  // digits of the next modulus while this one's MMAs run
+        const bool okm = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+        mph[0] ^= 1u;
         tc_fence_after();
-        const int k = i >> 1, part = i & 1;
         if (okm) {
-            float res[OPT];
-            const uint32_t tacc = tmem + lanebase + (uint32_t)(i & 1) * ACC_COLS + (uint32_t)(qd * OPT);
-            const int kind = fp8_kind(k);
-            if (kind == KIND_SQ)
-                read_classes<KIND_SQ, OPT>(tacc, NPAD, mc, k, res);
-            else if (kind == KIND_B9)
-                read_classes<KIND_B9, OPT>(tacc, NPAD, mc, k, res);
-            else
-                read_classes<KIND_B11, OPT>(tacc, NPAD, mc, k, res);
             const float mf = mc.fm[k], imf = mc.finv[k];
-            const int kk = part == 0 ? k : 12 + k;  // staging column: Re residues, then Im
-            const uint32_t koff = (uint32_t)(kk >> 3) * 128 + (uint32_t)(kk & 7) * 2;
-            float cv[OPT];
-            // canonical residue in [0, m) of the exact class sum (|res| < 2^24: the FP32
-            // quotient is within one of the true one, canon() fixes either side)
+            const int kind = fp8_kind(k);
 #pragma unroll
-            for (int o = 0; o < OPT; o++) cv[o] = canon(res[o], mf, imf);
+            for (int part = 0; part < 2; part++) {
+                float res[OPT];
+                const uint32_t tacc = tmem + lanebase + (uint32_t)part * ACC_COLS + (uint32_t)(qd * OPT);
+                if (kind == KIND_SQ)
+                    read_classes<KIND_SQ, OPT>(tacc, NPAD, mc, k, res);
+                else if (kind == KIND_B9)
+                    read_classes<KIND_B9, OPT>(tacc, NPAD, mc, k, res);
+                else
+                    read_classes<KIND_B11, OPT>(tacc, NPAD, mc, k, res);
+                const int kk = part == 0 ? k : 12 + k;  // staging column: Re residues, then Im
+                const uint32_t koff = (uint32_t)(kk >> 3) * 128 + (uint32_t)(kk & 7) * 2;
+                float cv[OPT];
+                // canonical residue in [0, m) of the exact class sum (|res| < 2^24: the FP32
+                // quotient is within one of the true one, canon() fixes either side)
 #pragma unroll
-            for (int o = 0; o + 1 < OPT; o += 2) {
-                const uint32_t hv = f16x2(cv[o], cv[o + 1]);  // exact: canonical residues < 2048
-                const int k0 = qd * OPT + o;
-                if (k0 < Kout)
-                    *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)k0 * 128 + c, 0) + koff) =
-                        (uint16_t)(hv & 0xFFFFu);
-                if (k0 + 1 < Kout)
-                    *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)(k0 + 1) * 128 + c, 0) + koff) =
-                        (uint16_t)(hv >> 16);
+                for (int o = 0; o < OPT; o++) cv[o] = canon(res[o], mf, imf);
+#pragma unroll
+                for (int o = 0; o + 1 < OPT; o += 2) {
+                    const uint32_t hv = f16x2(cv[o], cv[o + 1]);  // exact: canonical residues < 2048
+                    const int k0 = qd * OPT + o;
+                    if (k0 < Kout)
+                        *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)k0 * 128 + c, 0) + koff) =
+                            (uint16_t)(hv & 0xFFFFu);
+                    if (k0 + 1 < Kout)
+                        *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)(k0 + 1) * 128 + c, 0) + koff) =
+                            (uint16_t)(hv >> 16);
+                }
             }
         } else {
             atomicExch(&abort_flag, 1);
@@ -604,9 +608,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             ok = false;
             break;
         }
-        if (tid == 0 && i + 2 < NSTEP) {
+        if (tid == 0 && k + 1 < NSTEP) {
             tc_fence_after();
-            if (!issue(i + 2)) abort_flag = 1;
+            if (!issue(k + 1)) abort_flag = 1;
         }
         // an abort raised by issue() is seen after the next step's barrier
     }
@@ -678,7 +682,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
         // let in-flight MMAs drain (bounded) before the TMEM is freed
         mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
-        mbar_wait(smem_u32(&mbar[3]), mph[1], WAIT_LIMIT);
     }
     tc_fence_before();
     __syncthreads();
