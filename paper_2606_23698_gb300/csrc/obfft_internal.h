@@ -116,6 +116,7 @@ cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const S
 cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
 size_t fp8_smem_bytes(int Kout, int npad);
+cudaError_t fp8_upload_constants();  // once per device, outside any stream capture
 std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K);
 std::vector<uint8_t> build_phase_a_b();
 cudaError_t launch_stage_fp64(const AxisTables &t, const StageGeom &g, int stage,

@@ -382,6 +382,8 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
         e = upload(s1.data(), t.int8_s1_bytes, &t.int8_s1);
         if (e == cudaSuccess) e = upload(s2.data(), t.int8_s2_bytes, &t.int8_s2);
     } else if (P->mode == OBFFT_MODE_FP8) {
+        e = fp8_upload_constants();
+        if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP8 constants: ") + cudaGetErrorString(e));
         std::vector<uint8_t> s1 = build_fp8_planes(t.Fq, 1, t.q);
         std::vector<uint8_t> s2 = build_fp8_planes(t.Fp, t.q, t.p);
         e = upload(s1.data(), s1.size(), &t.fp8_s1);

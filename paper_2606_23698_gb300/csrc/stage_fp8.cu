@@ -257,6 +257,10 @@ __device__ __forceinline__ float canon(float x, float m, float im) {
 // per modulus: its MMAs run while the next modulus' digits are generated.
 // ---------------------------------------------------------------------------
 constexpr int FP8_WARPS = 16;
+
+// Per-modulus constants (identical for every plan): read through the constant
+// cache, uploaded once per device when the first FP8 plan is created.
+__constant__ ModConsts c_fp8_mc;
 constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 48, N_ABUF = 2;
 
 template <int NPAD>
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     constexpr int EPT = CF::EPT, OPT = CF::OPT, WPP = CF::WPP;
     constexpr int NSTEP = NMOD;  // one pipeline step per modulus
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ ModConsts mc;
+    const ModConsts &mc = c_fp8_mc;
     __shared__ int colpart[4][128];
     __shared__ __align__(8) uint64_t mbar[5];  // 0,1: B planes (TMA, per buffer), 2: MMA, 4: Phase-A B
     __shared__ uint32_t tmem_holder;
@@ -419,8 +423,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     uint8_t *sPAB = sB0 + 2 * 9 * planeB;
     const uint8_t *gplanes = planes + (size_t)group * FP8_PLANES_PER_GROUP * planeB;
 
-    for (int i = tid; i < (int)(sizeof(ModConsts) / 4); i += FP8_WARPS * 32)
-        reinterpret_cast<uint32_t *>(&mc)[i] = reinterpret_cast<const uint32_t *>(gmc)[i];
+    (void)gmc;
     if (tid < 32) reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[tid] = 0u;
     if (tid == 0) {
         abort_flag = 0;
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
         ok = __syncthreads_or(bad) == 0;  // uniform decision across the CTA
         const uint32_t idescA = instr_desc(128, PA_N, 0);
-        const int per_wave = 10;
+        const int per_wave = Kout % 8 == 0 ? 8 : 10;  // 8: two row blocks per quarter-warp per wave
         const uint32_t ebias[4] = {mc.kbias[0], mc.kbias[1], mc.kbias[2], mc.kbias[3]};
         const uint64_t zbias = ((uint64_t)mc.zbias[1] << 32) | mc.zbias[0];
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
@@ -686,6 +689,12 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     tc_fence_before();
     __syncthreads();
     if (w == 0) tmem_dealloc(tmem, 512);
+}
+
+cudaError_t fp8_upload_constants() {
+    ModConsts mc;
+    make_mod_consts(&mc);
+    return cudaMemcpyToSymbol(c_fp8_mc, &mc, sizeof(mc));
 }
 
 size_t fp8_smem_bytes(int Kout, int npad) {
