@@ -121,6 +121,24 @@ obfft_status obfft_exec_stage(obfft_plan p, int axis, int stage, const void *in,
                               void *stream);
 
 /*
+ * Device status of the plan: synchronises `stream` (a cudaStream_t), reads the
+ * plan's status word and returns OBFFT_ERR_TIMEOUT if a kernel's bounded wait
+ * on a tensor-core completion or a TMA copy gave up since the last call (the
+ * output of that transform is invalid), OBFFT_OK otherwise.  The word is reset.
+ * Not part of the paper: the kernels' waits have iteration limits so that a
+ * stalled wait ends with an error instead of hanging the GPU.
+ */
+obfft_status obfft_plan_status(obfft_plan p, void *stream);
+
+/*
+ * Exercise the failure path: launch a one-block kernel that waits, with a
+ * short iteration limit, on an mbarrier phase nothing completes, and records
+ * OBFFT_ERR_TIMEOUT in the plan's status word exactly as a stalled stage
+ * kernel would.  Nothing faults or hangs; obfft_plan_status then reports it.
+ */
+obfft_status obfft_selftest_bounded_wait(obfft_plan p, void *stream);
+
+/*
  * Host-only introspection (no GPU needed): the quantised constant
  * RNE(2^52 exp(dir 2 pi i m / N)) the plans use (Bailey paragraph and
  * Eq. twiddle-fusion: 53-bit signed significands, |re|, |im| <= 2^52), written

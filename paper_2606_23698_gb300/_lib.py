@@ -30,7 +30,7 @@ MODES = {"fp8": OBFFT_MODE_FP8, "int8": OBFFT_MODE_INT8, "fp64": OBFFT_MODE_FP64
 EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_splits",
            "obfft_plan_create_many", "obfft_exec_many", "obfft_exec_stage", "obfft_last_error",
            "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants",
-           "obfft_exec_fp64_noalloc")
+           "obfft_exec_fp64_noalloc", "obfft_plan_status", "obfft_selftest_bounded_wait")
 
 _lib = None
 
@@ -68,6 +68,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_host_twiddle.restype = i32
     L.obfft_host_crt_constants.argtypes = [vp, vp, vp, vp]
     L.obfft_host_crt_constants.restype = i32
+    L.obfft_plan_status.argtypes = [vp, vp]
+    L.obfft_plan_status.restype = i32
+    L.obfft_selftest_bounded_wait.argtypes = [vp, vp]
+    L.obfft_selftest_bounded_wait.restype = i32
     L.obfft_exec_fp64_noalloc.argtypes = [vp, vp, i64, i64, i64, i32, vp]
     L.obfft_exec_fp64_noalloc.restype = i32
     _lib = L
@@ -124,6 +128,15 @@ def obfft_exec_fp64_noalloc(in_ptr: int, out_ptr: int, n0: int, n1: int, n2: int
                             stream: int = 0) -> None:
     """Native-FP64 3-D transform that allocates nothing (scratch reserved at load)."""
     check(load().obfft_exec_fp64_noalloc(in_ptr, out_ptr, n0, n1, n2, dir, stream))
+
+
+def obfft_plan_status(plan: int, stream: int = 0) -> None:
+    """Raise ObfftError(OBFFT_ERR_TIMEOUT) if a device-side bounded wait gave up."""
+    check(load().obfft_plan_status(plan, stream))
+
+
+def obfft_selftest_bounded_wait(plan: int, stream: int = 0) -> None:
+    check(load().obfft_selftest_bounded_wait(plan, stream))
 
 
 def obfft_last_error() -> str:

@@ -117,6 +117,7 @@ cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const vo
                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
 size_t fp8_smem_bytes(int Kout, int npad);
 cudaError_t fp8_upload_constants();  // once per device, outside any stream capture
+cudaError_t launch_bounded_wait_selftest(int *status, cudaStream_t s);
 std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K);
 std::vector<uint8_t> build_phase_a_b();
 cudaError_t launch_stage_fp64(const AxisTables &t, const StageGeom &g, int stage,

@@ -822,6 +822,26 @@ extern "C" obfft_status obfft_exec_stage(obfft_plan p, int axis, int stage, cons
     return st;
 }
 
+extern "C" obfft_status obfft_plan_status(obfft_plan p, void *stream) {
+    if (!p) return set_error(OBFFT_ERR_ARG, "plan is NULL");
+    int v = 0, zero = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (v == OBFFT_OK) return OBFFT_OK;
+    cudaMemcpyAsync(p->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    return set_error((obfft_status)v, "a device-side bounded wait gave up (the transform's output is invalid)");
+}
+
+extern "C" obfft_status obfft_selftest_bounded_wait(obfft_plan p, void *stream) {
+    if (!p) return set_error(OBFFT_ERR_ARG, "plan is NULL");
+    cudaError_t e = launch_bounded_wait_selftest(p->d_status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
+    return OBFFT_OK;
+}
+
 extern "C" obfft_status obfft_host_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im) {
     if (N < 1 || !re || !im) return set_error(OBFFT_ERR_ARG, "bad argument");
     quantised_twiddle(m, N, dir, re, im);

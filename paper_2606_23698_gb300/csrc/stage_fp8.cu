@@ -9,7 +9,7 @@
 //   * the constant DFT / twiddle-fused matrix digits (planes of a_R, a_I and
 //     -a_I) arrive in shared memory by TMA bulk copy, double buffered;
 //   * the complex product is formed in real form, Re = a_R b_R + (-a_I) b_I and
-//     Im = a_I b_R + a_R b_I, as two pipelined steps per modulus: tcgen05.mma
+//     Im = a_I b_R + a_R b_I, in one pipelined step per modulus: tcgen05.mma
 //     kind::f8f6f4 (M = 128, N = 16/32, K = 32) accumulates each weight class of
 //     digit products in TMEM (FP32, every partial sum an integer below 2^17:
 //     exact).  On this GPU the tensor pipe has ample headroom and the SIMT
@@ -57,7 +57,6 @@ __host__ __device__ constexpr int fp8_plane_offset(int k) {
 }
 constexpr int FP8_PLANES_PER_GROUP = 81;  // 3 * (3*3 + 6*2 + 3*2)
 
-constexpr int FP8_THREADS = 256;
 constexpr int PA_N = 48;          // Phase A output columns (Re 24 | Im 24)
 constexpr int PA_ROWB = 384;      // bytes per 8-row group of the staging (3 K-chunks)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
@@ -70,23 +69,6 @@ struct ColMapT {
         if (c >= ncols) return false;
         if (stage == 2) return (c % Lpad) < L;
         return true;
-    }
-    __device__ __forceinline__ int64_t in_index(int64_t c, int j) const {
-        if (stage == 1) {
-            int64_t l = c / p, j1 = c % p;
-            return l * n + j1 + (int64_t)p * j;
-        }
-        int64_t k2 = c / Lpad, l = c % Lpad;
-        return l * n + k2 * p + j;
-    }
-    __device__ __forceinline__ int64_t out_index(int64_t c, int k) const {
-        if (stage == 1) {
-            int64_t l = c / p, j1 = c % p;
-            return l * n + (int64_t)k * p + j1;
-        }
-        int64_t k2 = c / Lpad, l = c % Lpad;
-        int64_t b = l / P, r = l % P;
-        return (b * n + k2 + (int64_t)q * k) * P + r;
     }
     __device__ __forceinline__ int group(int64_t c) const { return stage == 1 ? 0 : (int)(c / Lpad); }
     // element j of column c lives at ibase + j * istride; output k at obase + k * ostride
@@ -114,125 +96,6 @@ __device__ __forceinline__ uint32_t stage_off(uint32_t row, uint32_t k) {
     return (row >> 3) * PA_ROWB + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// E4M3 digit planes of balanced residues for one modulus: writes this thread's
-// 16 bytes (elements 16*hf .. 16*hf+15 of row c) of each digit plane.
-template <int KIND>
-__device__ __forceinline__ void write_digits(const float (&v)[16], uint8_t *sA, int c, int hf, float s) {
-    constexpr int ND = KIND == KIND_B11 ? 3 : 2;
-    uint32_t words[ND][4];
-#pragma unroll
-    for (int q4 = 0; q4 < 4; q4++) {
-        uint32_t pk[ND][2];
-#pragma unroll
-        for (int h2 = 0; h2 < 2; h2++) {
-            float dg[ND][2];
-#pragma unroll
-            for (int e2 = 0; e2 < 2; e2++) {
-                float x = v[q4 * 4 + h2 * 2 + e2];
-                if constexpr (KIND == KIND_SQ) {
-                    float h = rint_small(x * (1.0f / s));  // s h + l
-                    dg[0][e2] = h;
-                    dg[1][e2] = __fmaf_rn(-s, h, x);
-                } else if constexpr (KIND == KIND_B9) {
-                    float d1 = rint_small(x * 0.0625f);
-                    dg[1][e2] = d1;
-                    dg[0][e2] = __fmaf_rn(-16.0f, d1, x);
-                } else {
-                    float d2 = rint_small(x * 0.00390625f);
-                    float r = __fmaf_rn(-256.0f, d2, x);
-                    float d1 = rint_small(r * 0.0625f);
-                    dg[ND - 1][e2] = d2;
-                    dg[1][e2] = d1;
-                    dg[0][e2] = __fmaf_rn(-16.0f, d1, r);
-                }
-            }
-#pragma unroll
-            for (int d = 0; d < ND; d++) pk[d][h2] = e4m3x2(dg[d][0], dg[d][1]);
-        }
-#pragma unroll
-        for (int d = 0; d < ND; d++) words[d][q4] = pk[d][0] | (pk[d][1] << 16);
-    }
-    const uint32_t rowoff = (uint32_t)(c >> 3) * 256 + (uint32_t)hf * 128 + (uint32_t)(c & 7) * 16;
-#pragma unroll
-    for (int d = 0; d < ND; d++)
-        *reinterpret_cast<uint4 *>(sA + d * 4096 + rowoff) =
-            make_uint4(words[d][0], words[d][1], words[d][2], words[d][3]);
-}
-
-// Issue the digit-pair MMAs of one (modulus, product) into class accumulators.
-template <int KIND>
-__device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t sA, uint32_t sBp, int npad,
-                                               uint32_t idesc) {
-    const uint32_t planeB = (uint32_t)npad * 32;
-    auto mma = [&](int ci, int dj, int cls, uint32_t acc) {
-        uint64_t a = smem_desc(sA + dj * 4096, 128, 256);
-        uint64_t b = smem_desc(sBp + ci * planeB, 128, 256);
-        tc_mma_f8(tmem + cls * npad, a, b, idesc, acc);
-    };
-    if (KIND == KIND_SQ) {        // digits 0 = h, 1 = l
-        mma(0, 1, 1, 0);          // a_h b_l
-        mma(1, 0, 1, 1);          // a_l b_h
-        mma(1, 1, 0, 0);          // a_l b_l
-    } else if (KIND == KIND_B9) {
-        mma(0, 0, 0, 0);
-        mma(0, 1, 1, 0);
-        mma(1, 0, 1, 1);
-        mma(1, 1, 2, 0);
-    } else {
-        mma(0, 0, 0, 0);
-        mma(0, 1, 1, 0);
-        mma(1, 0, 1, 1);
-        mma(0, 2, 2, 0);
-        mma(1, 1, 2, 1);
-        mma(2, 0, 2, 1);
-        mma(1, 2, 3, 0);
-        mma(2, 1, 3, 1);
-        mma(2, 2, 4, 0);
-    }
-}
-
-// Read this thread's NH class accumulators (lane = row, columns hf*NH ..) and
-// recombine: returns the balanced residue of sum_j a_j b_j mod m.
-template <int KIND, int NH>
-__device__ __forceinline__ void read_product(uint32_t tlane, int npad, int hf, const ModConsts &mc, int k,
-                                             float (&out)[NH]) {
-    constexpr int NC = KIND == KIND_B11 ? 5 : (KIND == KIND_SQ ? 2 : 3);
-    float acc[NH];
-#pragma unroll
-    for (int i = 0; i < NH; i++) acc[i] = 0.f;
-    float wts[5];
-    if (KIND == KIND_SQ) {
-        wts[0] = 1.f;
-        wts[1] = mc.fsq[k];
-    } else {
-        wts[0] = 1.f;
-        wts[1] = 16.f;
-        wts[2] = 256.f;
-        wts[3] = mc.fc3[k];
-        wts[4] = mc.fc4[k];
-    }
-#pragma unroll
-    for (int cl = 0; cl < NC; cl++) {
-        uint32_t taddr = tlane + (uint32_t)(cl * npad + hf * NH);
-        if (NH == 16) {
-            uint32_t r[16];
-            tmem_ld16(taddr, r);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 16; i++) acc[i] = __fmaf_rn(wts[cl], __uint_as_float(r[i]), acc[i]);
-        } else {
-            uint32_t r[8];
-            tmem_ld8(taddr, r);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 8; i++) acc[i] = __fmaf_rn(wts[cl], __uint_as_float(r[i]), acc[i]);
-        }
-    }
-    const float m = mc.fm[k], im = mc.finv[k];
-#pragma unroll
-    for (int i = 0; i < NH; i++) out[i] = __fmaf_rn(-m, rint_small(acc[i] * im), acc[i]);
-}
-
 // canonical residue in [0, m) of an exact small integer x (|x| < 2^20), FP32
 __device__ __forceinline__ float canon(float x, float m, float im) {
     // q = rint(x / m) up to one unit near half-integers (FP32 quotient), so
@@ -247,10 +110,10 @@ __device__ __forceinline__ float canon(float x, float m, float im) {
 // Kernel: 512 threads.  Thread (sub = warp % 4, qd = warp / 4) owns TMEM lane
 // c = 32 sub + lane (= DFT column c of the tile), deconstructs elements
 // [EPT qd, EPT qd + EPT) of that column and finishes outputs [OPT qd, OPT qd +
-// OPT) of every product.  The (modulus, product) steps are software
-// pipelined: the digits of step i+1 are generated (into the other TMEM
-// A-buffer) while the MMAs of step i run; TMEM accumulators and the TMA-loaded
-// constant planes are double buffered.
+// OPT) of the Re and Im products.  The per-modulus steps are software
+// pipelined: the digits of modulus k+1 are generated (into the other TMEM
+// A-buffer) while the MMAs of modulus k run; the TMA-loaded constant planes
+// are double buffered.
 // TMEM columns: class accumulators of Re [0,160) and Im [160,320); A digit
 // planes of x_R (planes 0..2) and x_I (planes 3..5) of one modulus in two
 // buffers [320,368) and [368,416); Phase A reuses [0,480).  One pipeline step
@@ -689,6 +552,25 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     tc_fence_before();
     __syncthreads();
     if (w == 0) tmem_dealloc(tmem, 512);
+}
+
+// Failure-path self-test: waits (bounded) on an mbarrier phase that nothing
+// completes, then records OBFFT_ERR_TIMEOUT in the status word -- the same
+// path a real stalled wait takes, exercised without faulting or hanging.
+__global__ void bounded_wait_selftest_kernel(int *status, uint32_t limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(smem_u32(&bar), 0, limit);  // never arrives
+    if (!ok && threadIdx.x == 0) atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
+}
+
+cudaError_t launch_bounded_wait_selftest(int *status, cudaStream_t s) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(status, 1u << 12);
+    return cudaGetLastError();
 }
 
 cudaError_t fp8_upload_constants() {

@@ -200,3 +200,19 @@ def test_error_paths_on_device():
         _lib.obfft_exec(pl.handle, x.data_ptr() + 8, x.data_ptr(), -1, 0)  # misaligned
     with pytest.raises(ObfftError):
         _lib.obfft_exec(pl.handle, x.data_ptr(), x.data_ptr(), 0, 0)       # bad dir
+
+
+def test_device_timeout_reported_without_fault():
+    """Failure detection: a bounded wait that runs out reports OBFFT_ERR_TIMEOUT
+    through the plan status; the context stays usable afterwards."""
+    from paper_2606_23698_gb300 import ObfftError, _lib
+    pl = plan((8, 8, 8), "fp8")
+    _lib.obfft_plan_status(pl.handle)                       # clean
+    _lib.obfft_selftest_bounded_wait(pl.handle)
+    with pytest.raises(ObfftError) as ei:
+        _lib.obfft_plan_status(pl.handle)
+    assert ei.value.status == _lib.OBFFT_ERR_TIMEOUT
+    _lib.obfft_plan_status(pl.handle)                       # reset
+    x = S.complex_uniform(1, (8, 8, 8)).numpy()
+    y = run(pl, x)                                          # still works
+    assert bits_equal(y, oracle_full(x, splits_of(pl), -1))
