@@ -1,0 +1,42 @@
+"""One small, self-contained GPU invocation for profiler captures.
+
+    python -m paper_2606_23698_gb300.profile_case stage D0 D1 D2 AXIS STAGE MODE
+    python -m paper_2606_23698_gb300.profile_case fft3 D0 D1 D2 MODE
+
+`stage` runs a single stage launch (Bailey stage 1 or 2 of one axis pass) of a
+D0 x D1 x D2 plan on seeded uniform input; `fft3` runs one forward transform.
+Both print one line and exit 0, so the same command can run once plainly and
+then under a profiler restricted to the kernel of interest.
+"""
+import sys
+
+import torch
+
+from synth import inputs as S
+
+from .api import Plan
+
+
+def main(argv):
+    what = argv[0]
+    shape = tuple(int(v) for v in argv[1:4])
+    if what == "stage":
+        axis, stage, mode = int(argv[4]), int(argv[5]), argv[6]
+        x = S.complex_uniform(1, shape, device="cuda")
+        pl = Plan(*shape, mode=mode)
+        out = torch.empty_like(x)
+        pl.exec_stage(axis, stage, x, out)
+    elif what == "fft3":
+        mode = argv[4]
+        x = S.complex_uniform(1, shape, device="cuda")
+        pl = Plan(*shape, mode=mode)
+        out = torch.empty_like(x)
+        pl.exec(x, out)
+    else:
+        raise SystemExit(f"unknown case {what!r}")
+    torch.cuda.synchronize()
+    print("ok", what, shape, float(out.abs().sum()))
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
