@@ -46,8 +46,10 @@ def rne_div(v: np.ndarray, d: int) -> np.ndarray:
 
 
 def balanced(m: int) -> np.ndarray:
-    r = np.arange(m, dtype=np.int64)
-    return np.where(2 * r > m, r - m, r)
+    """Every integer v with |v| <= m/2: the balanced representatives of all
+    residues mod m, with both -m/2 and m/2 for even m (a round-half-even
+    reduction v = x - m RNE(x/m) can give either)."""
+    return np.arange(-(m // 2), m // 2 + 1, dtype=np.int64)
 
 
 def digits(m: int, v: np.ndarray):
@@ -105,11 +107,12 @@ def check_fp8_layout(m: int, K: int = 32) -> dict:
     b = v[None, :]
     da = [d[:, None] for d in dg]
     db = [d[None, :] for d in dg]
-    tot = np.zeros((m, m), dtype=np.int64)
+    n = v.size
+    tot = np.zeros((n, n), dtype=np.int64)
     for w, pl in pairs.items():
         cw = sum(da[i] * db[j] for i, j in pl)
         tot += wts[w] * cw
-    assert np.array_equal(np.mod(tot - a * b, m), np.zeros((m, m), np.int64)), m
+    assert np.array_equal(np.mod(tot - a * b, m), np.zeros((n, n), np.int64)), m
     return {"modulus": m, "kind": kind, "planes": nd, "mmas_per_product": sum(len(p) for p in pairs.values()),
             "classes": len(pairs), "max_digit": maxd, "max_combined": int(comb_max)}
 
