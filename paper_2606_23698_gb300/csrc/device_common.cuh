@@ -68,6 +68,13 @@ __device__ __forceinline__ uint32_t residue(const Pieces &pc, uint32_t m, uint32
     uint32_t t = pc.p0 + cneg + pc.p1 * c20 + pc.p2 * c40;  // < 2^32
     return barrett(t, m, mu);
 }
+// Lazily reduced residue: t - floor(t mu / 2^32) m lies in [0, 2m) for the
+// unbiased piece sum t = p0 + p1 2^20 + p2 2^40 (mod m) < 2^32 (no correction step).
+__device__ __forceinline__ uint32_t residue_lazy(const Pieces &pc, uint32_t m, uint32_t mu, uint32_t c20,
+                                                 uint32_t c40) {
+    uint32_t t = pc.p0 + pc.p1 * c20 + pc.p2 * c40;
+    return t - __umulhi(t, mu) * m;
+}
 // Canonical residue of a signed 32-bit value with |x| < 2^27.
 __device__ __forceinline__ uint32_t mod_signed27(int32_t x, uint32_t m, uint32_t mu, uint32_t off27) {
     return barrett((uint32_t)(x + (int32_t)off27), m, mu);

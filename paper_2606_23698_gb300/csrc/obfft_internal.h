@@ -20,6 +20,15 @@ constexpr int CT_COLS = 32;  // columns per CTA of the INT8 stage kernel
 extern const int kModuli[NMOD];
 
 // Per-modulus constants used on the device (one copy in __constant__ memory).
+// Offset added to the FP8 mode's reduced residues (|r| <= m/2 + 1) so that the
+// FP16 CRT operands are non-negative: r + RES_OFFSET lies in [2, 2046].
+constexpr int RES_OFFSET = 1024;
+
+// FP8-mode constant digit planes per matrix group: per modulus 4 planes per
+// digit (x_R half: a_R, a_I; x_I half: -a_I, a_R), 3 digits for the three
+// 11-bit moduli and 2 for the other nine.
+constexpr int FP8_PLANES_PER_GROUP = 4 * (3 * 3 + 9 * 2);
+
 struct ModConsts {
     uint32_t m[NMOD];         // moduli
     uint32_t barrett[NMOD];   // floor(2^32 / m)
@@ -36,12 +45,14 @@ struct ModConsts {
     // FP8-mode epilogue constants (exact small integers as floats)
     float fm[NMOD];    // m
     float finv[NMOD];  // 1/m rounded
-    float fhalf[NMOD]; // m/2
+    float foff[NMOD];  // -(2^23 + (2^55 mod m)): float bias of a lazily reduced data residue
     float fsq[NMOD];   // s for m = s^2, else 0
     float fc3[NMOD];   // 16^3 mod m
     float fc4[NMOD];   // 16^4 mod m
     // Kulisch deposit biases of the FP32-bit-pattern deposits:
-    // sum_{s<15} 0x4B000000 * 256^s mod 2^128 and sum_{t<6} 0x4B000000 * 256^t mod 2^64
+    // sum_{s<15} 0x4B000000 * 256^s + RES_OFFSET mod 2^128 (the CRT of residues
+    // r_k + RES_OFFSET lifts to C + RES_OFFSET, since sum_k u_k = 1 mod M) and
+    // sum_{t<6} 0x4B000000 * 256^t mod 2^64
     uint32_t kbias[4];
     uint32_t zbias[2];
 };

@@ -75,7 +75,7 @@ void make_mod_consts(ModConsts *mc) {
         mc->yk_over_mk[k] = (float)((double)y / (double)m);
         mc->fm[k] = (float)m;
         mc->finv[k] = (float)(1.0 / (double)m);
-        mc->fhalf[k] = (float)m * 0.5f;
+        mc->foff[k] = -(float)(8388608 + pow2_mod(55, m));
         int sq = 0;
         for (int t = 1; t * t <= (int)m; t++)
             if (t * t == (int)m) sq = t;
@@ -89,6 +89,7 @@ void make_mod_consts(ModConsts *mc) {
     }
     u128 kb = 0;
     for (int s = 0; s < S_RAW; s++) kb += (u128)0x4B000000u << (8 * s);  // wraps mod 2^128
+    kb += (u128)RES_OFFSET;
     for (int w = 0; w < 4; w++) mc->kbias[w] = (uint32_t)(kb >> (32 * w));
     uint64_t zb = 0;
     for (int t = 0; t < S_FRAC; t++) zb += (uint64_t)0x4B000000u << (8 * t);  // mod 2^64
@@ -294,32 +295,42 @@ static int fp8_digits(int k, int64_t v, int dig[3]) {
 }
 
 std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K) {
+    // Per modulus: for the x_R half, digit pairs (a_R digit, a_I digit); for
+    // the x_I half, (-a_I digit, a_R digit); digits in class order (squares:
+    // l before h).  Each plane is npad rows (outputs) x 32 bytes (K) in the
+    // no-swizzle K-major layout; a pair of planes is one N = 2 npad operand
+    // whose rows give the Re and Im accumulators side by side.
     const int npad = K <= 16 ? 16 : 32;
     const size_t planeB = (size_t)npad * 32;
-    std::vector<uint8_t> out((size_t)groups * 81 * planeB, 0);
+    std::vector<uint8_t> out((size_t)groups * FP8_PLANES_PER_GROUP * planeB, 0);
     size_t off = 0;
     for (int g = 0; g < groups; g++)
         for (int k = 0; k < NMOD; k++) {
             const int64_t m = kModuli[k];
             const int nd = k < 3 ? 3 : 2;
-            for (int p = 0; p < 3; p++) {
-                for (int n = 0; n < K; n++)
-                    for (int j = 0; j < K; j++) {
-                        const int64_t *e = &F[(((size_t)g * K + n) * K + j) * 2];
-                        // constant planes of the complex product in real form: a_R, a_I, -a_I
-                        int64_t a = p == 0 ? e[0] : p == 1 ? e[1] : -e[1];
-                        int64_t r = modc(a, m);
-                        int64_t v = 2 * r > m ? r - m : r;  // balanced
-                        int dig[3];
-                        fp8_digits(k, v, dig);
-                        for (int d = 0; d < nd; d++) {
-                            size_t pos = off + (size_t)(p * nd + d) * planeB + (size_t)(n / 8) * 256 +
-                                         (size_t)(j / 16) * 128 + (n % 8) * 16 + j % 16;
-                            out[pos] = e4m3_of_int(dig[d]);
-                        }
+            const bool square = k >= 3 && k < 9;
+            for (int h = 0; h < 2; h++)
+                for (int di = 0; di < nd; di++) {
+                    const int d = square ? 1 - di : di;  // digit index of this position
+                    for (int tb = 0; tb < 2; tb++) {
+                        // h = 0: (a_R, a_I); h = 1: (-a_I, a_R)
+                        const int sel = h == 0 ? (tb == 0 ? 0 : 1) : (tb == 0 ? 2 : 0);
+                        const size_t pbase = off + (size_t)((h * nd + di) * 2 + tb) * planeB;
+                        for (int n = 0; n < K; n++)
+                            for (int j = 0; j < K; j++) {
+                                const int64_t *e = &F[(((size_t)g * K + n) * K + j) * 2];
+                                const int64_t a = sel == 0 ? e[0] : sel == 1 ? e[1] : -e[1];
+                                const int64_t r = modc(a, m);
+                                const int64_t v = 2 * r > m ? r - m : r;  // balanced
+                                int dig[3];
+                                fp8_digits(k, v, dig);
+                                const size_t pos = pbase + (size_t)(n / 8) * 256 + (size_t)(j / 16) * 128 +
+                                                   (n % 8) * 16 + j % 16;
+                                out[pos] = e4m3_of_int(dig[d]);
+                            }
                     }
-            }
-            off += (size_t)3 * nd * planeB;
+                }
+            off += (size_t)4 * nd * planeB;
         }
     return out;
 }

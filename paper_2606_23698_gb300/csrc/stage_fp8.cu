@@ -2,24 +2,31 @@
 //
 // One CTA transforms 128 columns (one Ozaki-II complex GEMM per column,
 // Algorithm 1, one half).  Per modulus m_k:
-//   * the data residues (canonical x~ mod m_k, then balanced) of the real and
+//   * the data residues (x~ mod m_k, balanced) of the real and
 //     imaginary parts are split into E4M3-exact digit planes by the SIMT
 //     threads and written straight into tensor memory, where tcgen05.mma reads
 //     them as its A operand (row = column of the DFT, 32 bytes of K);
 //   * the constant DFT / twiddle-fused matrix digits (planes of a_R, a_I and
 //     -a_I) arrive in shared memory by TMA bulk copy, double buffered;
 //   * the complex product is formed in real form, Re = a_R b_R + (-a_I) b_I and
-//     Im = a_I b_R + a_R b_I, in one pipelined step per modulus: tcgen05.mma
-//     kind::f8f6f4 (M = 128, N = 16/32, K = 32) accumulates each weight class of
-//     digit products in TMEM (FP32, every partial sum an integer below 2^17:
-//     exact).  On this GPU the tensor pipe has ample headroom and the SIMT
-//     epilogue is the bottleneck, so the fourth real product is cheaper than the
-//     Karatsuba operand a_R + a_I and the residue-domain combine it would need
-//     (the INT8 mode keeps the paper's Karatsuba split);
+//     Im = a_I b_R + a_R b_I, in one pipelined step per modulus.  The constant
+//     operand stacks, along N, the Re and Im rows of every constant digit, so
+//     one tcgen05.mma kind::f8f6f4 (M = 128, N = 2 npad x digits, K = 32) per
+//     data digit and half (x_R or x_I) adds its digit products to a window of
+//     consecutive weight classes in TMEM (FP32, every partial sum an integer
+//     below 2^17: exact): 4 to 6 MMAs per modulus.  On this GPU the tensor pipe
+//     has ample headroom and the SIMT epilogue is the bottleneck, so the fourth
+//     real product is cheaper than the Karatsuba operand a_R + a_I and the
+//     residue-domain combine it would need (the INT8 mode keeps the paper's
+//     Karatsuba split);
 //   * the epilogue reads the classes back (tcgen05.ld), recombines them with
-//     their weights, reduces mod m_k to the canonical residue and writes the
-//     FP16 CRT operand (Sec. tcgarner: residues < 2048 are FP16-exact) to
-//     shared memory.
+//     their weights, reduces mod m_k to |r| <= m_k/2 + 1 and writes r + 1024
+//     as the FP16 CRT operand (Sec. tcgarner: integers below 2048 are
+//     FP16-exact) to shared memory.  Any representative of the residue class
+//     serves the CRT: sum_k u_k = 1 (mod M), so the offset lifts to C + 1024
+//     and is removed with the Kulisch bias constant.
+// The per-element and per-output arithmetic runs as packed two-lane FP32
+// (fma/add.f32x2), on the Re/Im parts of an element or on two outputs.
 // After the 12 moduli, CRT Phase A runs as tcgen05.mma kind::f16 (M = 128
 // complex outputs, N = 48 = Re/Im x (15 byte slices of u_k + 6 of w_k + 3
 // pad), K = 24 = Re/Im x 12 moduli, accumulators preset to 2^23, FP32
@@ -49,13 +56,14 @@ __host__ __device__ constexpr int fp8_ndig(int k) { return fp8_kind(k) == KIND_B
 __host__ __device__ constexpr int fp8_ncls(int k) {
     return fp8_kind(k) == KIND_B11 ? 5 : (fp8_kind(k) == KIND_SQ ? 2 : 3);
 }
-// planes before modulus k in a per-group table: sum_{k' < k} 3 * ndig(k')
+// planes before modulus k in a per-group table: sum_{k' < k} 4 * ndig(k')
 __host__ __device__ constexpr int fp8_plane_offset(int k) {
     int s = 0;
-    for (int i = 0; i < k; i++) s += 3 * fp8_ndig(i);
+    for (int i = 0; i < k; i++) s += 4 * fp8_ndig(i);
     return s;
 }
-constexpr int FP8_PLANES_PER_GROUP = 81;  // 3 * (3*3 + 6*2 + 3*2)
+static_assert(fp8_plane_offset(NMOD) == FP8_PLANES_PER_GROUP, "plane table size");
+constexpr int FP8_BPLANES = 12;  // planes of one modulus' constant operand buffer (at most 4 x 3)
 
 constexpr int PA_N = 48;          // Phase A output columns (Re 24 | Im 24)
 constexpr int PA_ROWB = 384;      // bytes per 8-row group of the staging (3 K-chunks)
@@ -96,14 +104,13 @@ __device__ __forceinline__ uint32_t stage_off(uint32_t row, uint32_t k) {
     return (row >> 3) * PA_ROWB + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// canonical residue in [0, m) of an exact small integer x (|x| < 2^20), FP32
-__device__ __forceinline__ float canon(float x, float m, float im) {
-    // q = rint(x / m) up to one unit near half-integers (FP32 quotient), so
-    // r = x - m q lies in (-m, m); the fix-ups map it to [0, m)
-    float q = rint_fma(x, im, 0.f);
-    float r = __fmaf_rn(-m, q, x);
-    r = r < 0.f ? r + m : r;
-    return r >= m ? r - m : r;
+// Reduced residue plus RES_OFFSET of two exact integers |x| < 2^24 (packed):
+// q = RNE(x / m) from the rounded reciprocal is within one of the true
+// quotient, so x - m q lies in [-m/2 - 1, m/2 + 1] and the offset value in
+// [2, 2046]: exact in FP16, non-negative for the biased Phase-A deposits.
+__device__ __forceinline__ float2 offset_residue2(float2 x, float2 nm, float2 im) {
+    const float2 q = rint2_mul(x, im);
+    return __fadd2_rn(__ffma2_rn(nm, q, x), f2splat((float)RES_OFFSET));
 }
 
 // ---------------------------------------------------------------------------
@@ -114,17 +121,18 @@ __device__ __forceinline__ float canon(float x, float m, float im) {
 // pipelined: the digits of modulus k+1 are generated (into the other TMEM
 // A-buffer) while the MMAs of modulus k run; the TMA-loaded constant planes
 // are double buffered.
-// TMEM columns: class accumulators of Re [0,160) and Im [160,320); A digit
-// planes of x_R (planes 0..2) and x_I (planes 3..5) of one modulus in two
-// buffers [320,368) and [368,416); Phase A reuses [0,480).  One pipeline step
-// per modulus: its MMAs run while the next modulus' digits are generated.
+// TMEM columns: class accumulators [0,320) (class cl: Re at cl 2 npad, Im at
+// cl 2 npad + npad); A digit planes of x_R (planes 0..2) and x_I (planes 3..5)
+// of one modulus in two buffers [320,368) and [368,416); Phase A reuses
+// [0,480).  One pipeline step per modulus: its MMAs run while the next
+// modulus' digits are generated.
 // ---------------------------------------------------------------------------
 constexpr int FP8_WARPS = 16;
 
 // Per-modulus constants (identical for every plan): read through the constant
 // cache, uploaded once per device when the first FP8 plan is created.
 __constant__ ModConsts c_fp8_mc;
-constexpr uint32_t ACC_COLS = 160, APL_BASE = 320, APL_COLS = 48, N_ABUF = 2;
+constexpr uint32_t APL_BASE = 320, APL_COLS = 48, N_ABUF = 2;
 
 template <int NPAD>
 struct Fp8Cfg {
@@ -133,107 +141,115 @@ struct Fp8Cfg {
     static constexpr int WPP = EPT / 4;   // 32-bit TMEM words per plane per thread
 };
 
-// digits of EPT balanced residues -> E4M3 words of up to 3 planes
+// Digits of EPT balanced residue pairs (x_R, x_I) -> E4M3 words of up to 3
+// planes each for x_R (wR) and x_I (wI); the digit arithmetic runs packed on
+// both parts of an element.
 template <int KIND, int EPT>
-__device__ __forceinline__ void digits_to_words(const float (&v)[EPT], float s, uint32_t (&wd)[3][EPT / 4]) {
+__device__ __forceinline__ void digits_to_words2(const float2 (&v)[EPT], float s, uint32_t (&wR)[3][EPT / 4],
+                                                 uint32_t (&wI)[3][EPT / 4]) {
+    float2 dg[3][EPT];
 #pragma unroll
-    for (int q4 = 0; q4 < EPT / 4; q4++) {
-        uint32_t pk[3][2];
-#pragma unroll
-        for (int h2 = 0; h2 < 2; h2++) {
-            float dg[3][2];
-#pragma unroll
-            for (int e2 = 0; e2 < 2; e2++) {
-                float x = v[q4 * 4 + h2 * 2 + e2];
-                if constexpr (KIND == KIND_SQ) {
-                    float h = rint_fma(x, 1.0f / s, 0.f);
-                    dg[0][e2] = h;
-                    dg[1][e2] = __fmaf_rn(-s, h, x);
-                    dg[2][e2] = 0.f;
-                } else if constexpr (KIND == KIND_B9) {
-                    float d1 = rint_fma(x, 0.0625f, 0.f);
-                    dg[1][e2] = d1;
-                    dg[0][e2] = __fmaf_rn(-16.0f, d1, x);
-                    dg[2][e2] = 0.f;
-                } else {
-                    float d2 = rint_fma(x, 0.00390625f, 0.f);
-                    float r = __fmaf_rn(-256.0f, d2, x);
-                    float d1 = rint_fma(r, 0.0625f, 0.f);
-                    dg[2][e2] = d2;
-                    dg[1][e2] = d1;
-                    dg[0][e2] = __fmaf_rn(-16.0f, d1, r);
-                }
-            }
-#pragma unroll
-            for (int d = 0; d < 3; d++) pk[d][h2] = e4m3x2(dg[d][0], dg[d][1]);
+    for (int j = 0; j < EPT; j++) {
+        const float2 x = v[j];
+        if constexpr (KIND == KIND_SQ) {
+            const float2 h = rint2_mul(x, f2splat(1.0f / s));
+            dg[0][j] = h;
+            dg[1][j] = __ffma2_rn(f2splat(-s), h, x);
+        } else if constexpr (KIND == KIND_B9) {
+            const float2 d1 = rint2_mul(x, f2splat(0.0625f));
+            dg[1][j] = d1;
+            dg[0][j] = __ffma2_rn(f2splat(-16.0f), d1, x);
+        } else {
+            const float2 d2 = rint2_mul(x, f2splat(0.00390625f));
+            const float2 r = __ffma2_rn(f2splat(-256.0f), d2, x);
+            const float2 d1 = rint2_mul(r, f2splat(0.0625f));
+            dg[2][j] = d2;
+            dg[1][j] = d1;
+            dg[0][j] = __ffma2_rn(f2splat(-16.0f), d1, r);
         }
-#pragma unroll
-        for (int d = 0; d < 3; d++) wd[d][q4] = pk[d][0] | (pk[d][1] << 16);
     }
+    constexpr int ND = KIND == KIND_B11 ? 3 : 2;
+#pragma unroll
+    for (int d = 0; d < ND; d++)
+#pragma unroll
+        for (int q4 = 0; q4 < EPT / 4; q4++) {
+            const int j = 4 * q4;
+            wR[d][q4] = e4m3x2(dg[d][j].x, dg[d][j + 1].x) | (e4m3x2(dg[d][j + 2].x, dg[d][j + 3].x) << 16);
+            wI[d][q4] = e4m3x2(dg[d][j].y, dg[d][j + 1].y) | (e4m3x2(dg[d][j + 2].y, dg[d][j + 3].y) << 16);
+        }
 }
 
-// Digit-pair MMAs of one (modulus, part) step of the complex product in real
-// form: Re = sum a_R b_R + (-a_I) b_I, Im = sum a_I b_R + a_R b_I.  Constant
-// planes per modulus: [a_R digits][a_I digits][-a_I digits]; data planes in the
-// A buffer: [b_R digits (planes 0..2)][b_I digits (planes 3..5)].  Each weight
-// class of digit pairs accumulates in one TMEM accumulator (K = 2 x 32 terms).
+// MMAs of one modulus, complex product in real form with the Re and Im
+// outputs side by side along N: for the x_R half the constant rows are
+// (a_R, a_I) per digit, for the x_I half (-a_I, a_R), so each MMA adds
+// a_R b_R and a_I b_R (or -a_I b_I and a_R b_I) to the Re and Im columns of
+// consecutive weight classes.  One MMA per data digit and half: its constant
+// operand holds every constant digit (in class order), its accumulator window
+// starts at the class of the data digit.  TMEM accumulator of class cl:
+// columns [cl 2 npad, cl 2 npad + npad) Re, [.. + npad, .. + 2 npad) Im.
+// Classes the window reaches beyond the first MMA's (B9: 2, B11: 3 and 4)
+// must hold zero when the modulus starts.
 template <int KIND>
-__device__ __forceinline__ void issue_part_ta(uint32_t dacc, uint32_t apl, uint64_t bdesc, int npad, int part,
-                                              uint32_t idesc) {
+__device__ __forceinline__ void issue_modulus_nm(uint32_t dacc, uint32_t apl, uint64_t bdesc, int npad) {
     constexpr int ND = KIND == KIND_B11 ? 3 : 2;
     const uint32_t planeB16 = (uint32_t)npad * 2;  // plane size in 16-byte descriptor units
-    // constant operand for the x_R half and the x_I half of this part
-    const int cR = part == 0 ? 0 : 1;  // a_R (Re) or a_I (Im)
-    const int cI = part == 0 ? 2 : 0;  // -a_I (Re) or a_R (Im)
-    auto mma2 = [&](int ci, int dj, int cls, uint32_t first) {
-        tc_mma_f8_ta(dacc + cls * npad, apl + dj * 8, bdesc + (uint64_t)((cR * ND + ci) * planeB16), idesc,
-                     first ? 0u : 1u);
-        tc_mma_f8_ta(dacc + cls * npad, apl + (3 + dj) * 8, bdesc + (uint64_t)((cI * ND + ci) * planeB16), idesc,
-                     1u);
-    };
-    if (KIND == KIND_SQ) {  // digits 0 = h, 1 = l
-        mma2(0, 1, 1, 1);
-        mma2(1, 0, 1, 0);
-        mma2(1, 1, 0, 1);
-    } else if (KIND == KIND_B9) {
-        mma2(0, 0, 0, 1);
-        mma2(0, 1, 1, 1);
-        mma2(1, 0, 1, 0);
-        mma2(1, 1, 2, 1);
-    } else {
-        mma2(0, 0, 0, 1);
-        mma2(0, 1, 1, 1);
-        mma2(1, 0, 1, 0);
-        mma2(0, 2, 2, 1);
-        mma2(1, 1, 2, 0);
-        mma2(2, 0, 2, 0);
-        mma2(1, 2, 3, 1);
-        mma2(2, 1, 3, 0);
-        mma2(2, 2, 4, 1);
+    const uint32_t cls = 2u * (uint32_t)npad;       // TMEM columns per class
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const uint64_t bh = bdesc + (uint64_t)(h * 2 * ND) * planeB16;
+        const uint32_t ah = apl + (uint32_t)(3 * h) * 8;  // data planes of x_R (h = 0) or x_I (h = 1)
+        if (KIND == KIND_SQ) {  // data digit 0 = h, 1 = l; constant rows [l pair, h pair]
+            tc_mma_f8_ta(dacc, ah + 8, bh, instr_desc(128, 4 * npad, 0), h ? 1u : 0u);  // classes 1, s
+            tc_mma_f8_ta(dacc + cls, ah, bh, instr_desc(128, 2 * npad, 0), 1u);        // class s
+        } else {
+#pragma unroll
+            for (int dj = 0; dj < ND; dj++)
+                tc_mma_f8_ta(dacc + (uint32_t)dj * cls, ah + (uint32_t)dj * 8, bh,
+                             instr_desc(128, 2 * ND * npad, 0), (h == 0 && dj == 0) ? 0u : 1u);
+        }
     }
 }
 
-// class accumulators of this thread's OPT outputs -> their weighted sum (exact)
+constexpr int fp8_ncls_of_kind(int kind) { return kind == KIND_B11 ? 5 : (kind == KIND_SQ ? 2 : 3); }
+
+// Issue the TMEM loads of the class accumulators of this thread's OPT outputs
+// (completion: tmem_wait_ld, then regs_after_wait).
 template <int KIND, int OPT>
-__device__ __forceinline__ void read_classes(uint32_t tacc, int npad, const ModConsts &mc, int k,
-                                             float (&out)[OPT]) {
-    constexpr int NC = KIND == KIND_B11 ? 5 : (KIND == KIND_SQ ? 2 : 3);
-    uint32_t r[NC][OPT];
+__device__ __forceinline__ void load_classes(uint32_t tacc, int npad, uint32_t (&r)[5][OPT]) {
 #pragma unroll
-    for (int cl = 0; cl < NC; cl++) {
-        if constexpr (OPT == 8) {
-            uint32_t t[8];
-            tmem_ld8(tacc + cl * npad, t);
-#pragma unroll
-            for (int i = 0; i < 8; i++) r[cl][i] = t[i];
-        } else {
-            uint32_t t[4];
-            tmem_ld4(tacc + cl * npad, t);
-#pragma unroll
-            for (int i = 0; i < 4; i++) r[cl][i] = t[i];
-        }
+    for (int cl = 0; cl < fp8_ncls_of_kind(KIND); cl++) {
+        if constexpr (OPT == 8)
+            tmem_ld8(tacc + cl * 2 * npad, r[cl]);
+        else
+            tmem_ld4(tacc + cl * 2 * npad, r[cl]);
     }
-    tmem_wait_ld();
+}
+// Zero this thread's columns of the classes >= 2 (they must start the next
+// modulus at zero, see issue_modulus_nm).
+template <int KIND, int OPT>
+__device__ __forceinline__ void zero_high_classes(uint32_t tacc, int npad) {
+#pragma unroll
+    for (int cl = 2; cl < fp8_ncls_of_kind(KIND); cl++) {
+        if constexpr (OPT == 8)
+            tmem_st8_const(tacc + cl * 2 * npad, 0u);
+        else
+            tmem_st4_const(tacc + cl * 2 * npad, 0u);
+    }
+}
+// Orders every later use of the loaded registers after the preceding tcgen05.wait::ld.
+template <int KIND, int OPT>
+__device__ __forceinline__ void regs_after_wait(uint32_t (&r)[5][OPT]) {
+#pragma unroll
+    for (int cl = 0; cl < fp8_ncls_of_kind(KIND); cl++)
+#pragma unroll
+        for (int i = 0; i < OPT; i++) asm volatile("" : "+r"(r[cl][i]));
+}
+// Class values -> their weighted sums (exact integers, |a| < 2^24, congruent
+// to sum_j a_j b_j mod m), as packed pairs of consecutive outputs.
+template <int KIND, int OPT>
+__device__ __forceinline__ void combine_classes(const uint32_t (&r)[5][OPT], const ModConsts &mc, int k,
+                                                float2 (&out)[OPT / 2]) {
+    constexpr int NC = fp8_ncls_of_kind(KIND);
     float wts[5];
     if constexpr (KIND == KIND_SQ) {
         wts[0] = 1.f;
@@ -246,11 +262,53 @@ __device__ __forceinline__ void read_classes(uint32_t tacc, int npad, const ModC
         wts[4] = mc.fc4[k];
     }
 #pragma unroll
-    for (int i = 0; i < OPT; i++) {
-        float a = __uint_as_float(r[0][i]);
+    for (int i = 0; i < OPT / 2; i++) {
+        float2 a = make_float2(__uint_as_float(r[0][2 * i]), __uint_as_float(r[0][2 * i + 1]));
 #pragma unroll
-        for (int cl = 1; cl < NC; cl++) a = __fmaf_rn(wts[cl], __uint_as_float(r[cl][i]), a);
-        out[i] = a;  // exact integer, |a| < 2^24, congruent to sum_j a_j b_j mod m
+        for (int cl = 1; cl < NC; cl++)
+            a = __ffma2_rn(f2splat(wts[cl]),
+                           make_float2(__uint_as_float(r[cl][2 * i]), __uint_as_float(r[cl][2 * i + 1])), a);
+        out[i] = a;
+    }
+}
+
+// Epilogue of modulus k for this thread's OPT outputs of the Re and Im
+// products: offset residues as FP16 into the Phase-A staging.  The loads of
+// the Im classes are in flight while the Re residues are reduced and stored.
+template <int KIND, int OPT>
+__device__ __forceinline__ void epilogue_modulus(uint32_t tacc_re, uint32_t tacc_im, int npad, const ModConsts &mc,
+                                                 int k, uint8_t *sStage, int c, int qd, int Kout) {
+    const float2 nm2 = f2splat(-mc.fm[k]), im2 = f2splat(mc.finv[k]);
+    uint32_t r[5][OPT];
+    float2 res[OPT / 2];
+    load_classes<KIND, OPT>(tacc_re, npad, r);
+    tmem_wait_ld();
+    regs_after_wait<KIND, OPT>(r);
+    combine_classes<KIND, OPT>(r, mc, k, res);
+    zero_high_classes<KIND, OPT>(tacc_re, npad);
+#pragma unroll
+    for (int part = 0; part < 2; part++) {
+        if (part == 0) load_classes<KIND, OPT>(tacc_im, npad, r);
+        const int kk = part == 0 ? k : 12 + k;  // staging column: Re residues, then Im
+        const uint32_t koff = (uint32_t)(kk >> 3) * 128 + (uint32_t)(kk & 7) * 2;
+#pragma unroll
+        for (int o2 = 0; o2 < OPT / 2; o2++) {
+            const float2 cv = offset_residue2(res[o2], nm2, im2);
+            const uint32_t hv = f16x2(cv.x, cv.y);  // exact: offset residues in [2, 2046]
+            const int k0 = qd * OPT + 2 * o2;
+            if (k0 < Kout)
+                *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)k0 * 128 + c, 0) + koff) =
+                    (uint16_t)(hv & 0xFFFFu);
+            if (k0 + 1 < Kout)
+                *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)(k0 + 1) * 128 + c, 0) + koff) =
+                    (uint16_t)(hv >> 16);
+        }
+        if (part == 0) {
+            tmem_wait_ld();
+            regs_after_wait<KIND, OPT>(r);
+            combine_classes<KIND, OPT>(r, mc, k, res);
+            zero_high_classes<KIND, OPT>(tacc_im, npad);
+        }
     }
 }
 
@@ -283,7 +341,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     uint8_t *sStage = smem;
     uint8_t *sB0 = smem + ((stage_bytes + 1023) & ~1023u);
     const uint32_t planeB = NPAD * 32;
-    uint8_t *sPAB = sB0 + 2 * 9 * planeB;
+    uint8_t *sPAB = sB0 + 2 * FP8_BPLANES * planeB;
     const uint8_t *gplanes = planes + (size_t)group * FP8_PLANES_PER_GROUP * planeB;
 
     (void)gmc;
@@ -301,10 +359,21 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     if (tid == 0) {
         mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
         tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
-        const uint32_t bytes0 = 3 * fp8_ndig(0) * planeB;
+        const uint32_t bytes0 = 4 * fp8_ndig(0) * planeB;
         mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
         tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
     }
+    // classes 2..4 start at zero (issue_modulus_nm)
+#pragma unroll
+    for (int cl = 2; cl < 5; cl++)
+#pragma unroll
+        for (int part = 0; part < 2; part++) {
+            const uint32_t ta = tmem + lanebase + (uint32_t)(cl * 2 * NPAD + part * NPAD + qd * OPT);
+            if constexpr (OPT == 8)
+                tmem_st8_const(ta, 0u);
+            else
+                tmem_st4_const(ta, 0u);
+        }
     // K <= 16: bytes 16..31 of every A row stay zero (columns 4..7 of each of the 6 planes)
     if (NPAD == 16 && qd == 0) {
 #pragma unroll
@@ -347,29 +416,28 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
 
     // digits of x_R and x_I for modulus k into A buffer (k & 1)
     auto gen = [&](int k) {
-        const float mf = mc.fm[k];
-        const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k], cn = mc.c55neg[k];
-        const float halfm = mc.fhalf[k];
-        float vR[EPT], vI[EPT];
+        const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k];
+        const float2 nm2 = f2splat(-mc.fm[k]), im2 = f2splat(mc.finv[k]), off2 = f2splat(mc.foff[k]);
+        float2 v[EPT];
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
-            float fr = __uint_as_float(0x4B000000u | residue(pR[jj], m, mu, c20, c40, cn)) - 8388608.0f;
-            float fi = __uint_as_float(0x4B000000u | residue(pI[jj], m, mu, c20, c40, cn)) - 8388608.0f;
-            vR[jj] = fr > halfm ? fr - mf : fr;  // balanced
-            vI[jj] = fi > halfm ? fi - mf : fi;
+            // lazily reduced residues in [0, 2m) of x~ + 2^55; as floats minus 2^55 mod m
+            // they lie in (-m, 2m), and one packed rounding step balances them exactly
+            // (the quotients are below 3, far from FP32 rounding trouble)
+            const uint32_t rR = residue_lazy(pR[jj], m, mu, c20, c40);
+            const uint32_t rI = residue_lazy(pI[jj], m, mu, c20, c40);
+            float2 f = make_float2(__uint_as_float(0x4B000000u | rR), __uint_as_float(0x4B000000u | rI));
+            f = __fadd2_rn(f, off2);
+            v[jj] = __ffma2_rn(nm2, rint2_mul(f, im2), f);  // balanced, [-m/2, m/2]
         }
         uint32_t wR[3][WPP], wI[3][WPP];
         const int kind = fp8_kind(k);
-        if (kind == KIND_SQ) {
-            digits_to_words<KIND_SQ, EPT>(vR, mc.fsq[k], wR);
-            digits_to_words<KIND_SQ, EPT>(vI, mc.fsq[k], wI);
-        } else if (kind == KIND_B9) {
-            digits_to_words<KIND_B9, EPT>(vR, 0.f, wR);
-            digits_to_words<KIND_B9, EPT>(vI, 0.f, wI);
-        } else {
-            digits_to_words<KIND_B11, EPT>(vR, 0.f, wR);
-            digits_to_words<KIND_B11, EPT>(vI, 0.f, wI);
-        }
+        if (kind == KIND_SQ)
+            digits_to_words2<KIND_SQ, EPT>(v, mc.fsq[k], wR, wI);
+        else if (kind == KIND_B9)
+            digits_to_words2<KIND_B9, EPT>(v, 0.f, wR, wI);
+        else
+            digits_to_words2<KIND_B11, EPT>(v, 0.f, wR, wI);
         const uint32_t ta = tmem + lanebase + APL_BASE + (uint32_t)(k & 1) * APL_COLS + (uint32_t)(qd * WPP);
         const int nd = fp8_ndig(k);
 #pragma unroll
@@ -389,29 +457,24 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // modulus k live in B buffer k & 1; B(k+1) is prefetched here, into the
     // buffer of modulus k-1, whose MMAs have completed.
     const uint64_t bdesc0 = smem_desc(smem_u32(sB0), 128, 256);
-    const uint64_t bdesc1 = smem_desc(smem_u32(sB0 + 9 * planeB), 128, 256);
+    const uint64_t bdesc1 = smem_desc(smem_u32(sB0 + FP8_BPLANES * planeB), 128, 256);
     auto issue = [&](int k) -> bool {
         if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
         if (k + 1 < NMOD) {
-            const uint32_t bytes = 3 * fp8_ndig(k + 1) * planeB;
+            const uint32_t bytes = 4 * fp8_ndig(k + 1) * planeB;
             mbar_expect_tx(smem_u32(&mbar[(k + 1) & 1]), bytes);
-            tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * 9 * planeB),
+            tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * FP8_BPLANES * planeB),
                          gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes, smem_u32(&mbar[(k + 1) & 1]));
         }
-        const uint32_t idesc = instr_desc(128, NPAD, 0);
         const uint64_t bd = (k & 1) ? bdesc1 : bdesc0;
         const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * APL_COLS;
         const int kind = fp8_kind(k);
-#pragma unroll
-        for (int part = 0; part < 2; part++) {
-            const uint32_t dacc = tmem + (uint32_t)part * ACC_COLS;
-            if (kind == KIND_SQ)
-                issue_part_ta<KIND_SQ>(dacc, apl, bd, NPAD, part, idesc);
-            else if (kind == KIND_B9)
-                issue_part_ta<KIND_B9>(dacc, apl, bd, NPAD, part, idesc);
-            else
-                issue_part_ta<KIND_B11>(dacc, apl, bd, NPAD, part, idesc);
-        }
+        if (kind == KIND_SQ)
+            issue_modulus_nm<KIND_SQ>(tmem, apl, bd, NPAD);
+        else if (kind == KIND_B9)
+            issue_modulus_nm<KIND_B9>(tmem, apl, bd, NPAD);
+        else
+            issue_modulus_nm<KIND_B11>(tmem, apl, bd, NPAD);
         tc_commit(smem_u32(&mbar[2]));
         return true;
     };
@@ -433,37 +496,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         mph[0] ^= 1u;
         tc_fence_after();
         if (okm) {
-            const float mf = mc.fm[k], imf = mc.finv[k];
+            const uint32_t tre = tmem + lanebase + (uint32_t)(qd * OPT);
             const int kind = fp8_kind(k);
-#pragma unroll
-            for (int part = 0; part < 2; part++) {
-                float res[OPT];
-                const uint32_t tacc = tmem + lanebase + (uint32_t)part * ACC_COLS + (uint32_t)(qd * OPT);
-                if (kind == KIND_SQ)
-                    read_classes<KIND_SQ, OPT>(tacc, NPAD, mc, k, res);
-                else if (kind == KIND_B9)
-                    read_classes<KIND_B9, OPT>(tacc, NPAD, mc, k, res);
-                else
-                    read_classes<KIND_B11, OPT>(tacc, NPAD, mc, k, res);
-                const int kk = part == 0 ? k : 12 + k;  // staging column: Re residues, then Im
-                const uint32_t koff = (uint32_t)(kk >> 3) * 128 + (uint32_t)(kk & 7) * 2;
-                float cv[OPT];
-                // canonical residue in [0, m) of the exact class sum (|res| < 2^24: the FP32
-                // quotient is within one of the true one, canon() fixes either side)
-#pragma unroll
-                for (int o = 0; o < OPT; o++) cv[o] = canon(res[o], mf, imf);
-#pragma unroll
-                for (int o = 0; o + 1 < OPT; o += 2) {
-                    const uint32_t hv = f16x2(cv[o], cv[o + 1]);  // exact: canonical residues < 2048
-                    const int k0 = qd * OPT + o;
-                    if (k0 < Kout)
-                        *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)k0 * 128 + c, 0) + koff) =
-                            (uint16_t)(hv & 0xFFFFu);
-                    if (k0 + 1 < Kout)
-                        *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)(k0 + 1) * 128 + c, 0) + koff) =
-                            (uint16_t)(hv >> 16);
-                }
-            }
+            if (kind == KIND_SQ)
+                epilogue_modulus<KIND_SQ, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+            else if (kind == KIND_B9)
+                epilogue_modulus<KIND_B9, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+            else
+                epilogue_modulus<KIND_B11, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
         } else {
             atomicExch(&abort_flag, 1);
         }
@@ -581,7 +621,7 @@ cudaError_t fp8_upload_constants() {
 
 size_t fp8_smem_bytes(int Kout, int npad) {
     size_t stage_bytes = (size_t)Kout * 128 / 8 * PA_ROWB + 128;
-    return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * 9 * (size_t)npad * 32 + PA_N * 64;
+    return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * FP8_BPLANES * (size_t)npad * 32 + PA_N * 64;
 }
 
 cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,

@@ -139,6 +139,13 @@ __device__ __forceinline__ void tmem_st16_const(uint32_t taddr, uint32_t v) {
         "r"(v)
         : "memory");
 }
+__device__ __forceinline__ void tmem_st8_const(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(v)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st4_const(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%1,%1,%1};" ::"r"(taddr), "r"(v) : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -167,6 +174,13 @@ __device__ __forceinline__ float rint_small(float x) {
 // RNE integer of a * b + c for |a b + c| < 2^22 (fused, one rounding before the magic add)
 __device__ __forceinline__ float rint_fma(float a, float b, float c) {
     return __fadd_rn(__fmaf_rn(a, b, c + 12582912.0f), -12582912.0f);
+}
+
+// Packed two-lane FP32 arithmetic (one instruction for both lanes).
+__device__ __forceinline__ float2 f2splat(float v) { return make_float2(v, v); }
+// RNE integers of a * b for both lanes, |a b| < 2^22 (fused, then magic add)
+__device__ __forceinline__ float2 rint2_mul(float2 a, float2 b) {
+    return __fadd2_rn(__ffma2_rn(a, b, f2splat(12582912.0f)), f2splat(-12582912.0f));
 }
 
 }  // namespace obfft
