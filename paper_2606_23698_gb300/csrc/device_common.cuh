@@ -249,4 +249,101 @@ __device__ __forceinline__ double kulisch_pack_fp8(const uint32_t *wv, const Mod
     return __longlong_as_double((long long)bits);
 }
 
+// Straight-line form of the common case of kulisch_pack_fp8, for two outputs
+// computed side by side: no early exits, so the compiler can interleave the
+// chains.  Sets `slow` (and returns an unspecified value) when the general
+// finish is needed: lift near a rounding boundary, |R| < 2^64, or a result
+// that is subnormal or overflows; Rw (R = E - bias - zhat M mod 2^128) and
+// near_out then feed kulisch_finish_general.  Otherwise the result equals
+// kulisch_pack_fp8's bit for bit.
+__device__ __forceinline__ double kulisch_pack_fp8_fast(const uint32_t *wv, const ModConsts &mc, int et,
+                                                        const uint32_t (&ebias)[4], uint64_t zbias, bool &slow,
+                                                        uint32_t (&Rw)[4], bool &near_out) {
+    uint64_t a0 = (uint64_t)wv[0];
+    a0 += (uint64_t)wv[1] * 256u;
+    a0 += (uint64_t)wv[2] * 65536u;
+    a0 += (uint64_t)wv[3] * 16777216u;
+    uint64_t a1 = (uint64_t)wv[4];
+    a1 += (uint64_t)wv[5] * 256u;
+    a1 += (uint64_t)wv[6] * 65536u;
+    a1 += (uint64_t)wv[7] * 16777216u;
+    uint64_t a2 = (uint64_t)wv[8];
+    a2 += (uint64_t)wv[9] * 256u;
+    a2 += (uint64_t)wv[10] * 65536u;
+    a2 += (uint64_t)wv[11] * 16777216u;
+    uint64_t a3 = (uint64_t)wv[12];
+    a3 += (uint64_t)wv[13] * 256u;
+    a3 += (uint64_t)wv[14] * 65536u;
+    const uint32_t w0 = (uint32_t)a0;
+    uint64_t t = (a0 >> 32) + a1;
+    const uint32_t w1 = (uint32_t)t;
+    t = (t >> 32) + a2;
+    const uint32_t w2 = (uint32_t)t;
+    t = (t >> 32) + a3;
+    const uint32_t w3 = (uint32_t)t;
+    uint64_t z = (uint64_t)wv[15] + (uint64_t)wv[16] * 256u + (uint64_t)wv[17] * 65536u +
+                 (uint64_t)wv[18] * 16777216u + ((uint64_t)wv[19] << 32) + ((uint64_t)wv[20] << 40);
+    z -= zbias;
+    const uint64_t zr = z + (1ull << 47);
+    const uint32_t zhat = (uint32_t)(zr >> 48);
+    const uint64_t frac = zr & ((1ull << 48) - 1);
+    uint64_t p0 = (uint64_t)zhat * mc.M32[0];
+    uint64_t p1 = (uint64_t)zhat * mc.M32[1] + (p0 >> 32);
+    uint64_t p2 = (uint64_t)zhat * mc.M32[2] + (p1 >> 32);
+    uint32_t p3 = zhat * mc.M32[3] + (uint32_t)(p2 >> 32);
+    uint32_t s0, s1, s2, s3, r0, r1, r2, r3;
+    asm("add.cc.u32 %0, %4, %8;\n\taddc.cc.u32 %1, %5, %9;\n\taddc.cc.u32 %2, %6, %10;\n\taddc.u32 %3, %7, %11;"
+        : "=r"(s0), "=r"(s1), "=r"(s2), "=r"(s3)
+        : "r"((uint32_t)p0), "r"((uint32_t)p1), "r"((uint32_t)p2), "r"(p3), "r"(ebias[0]), "r"(ebias[1]),
+          "r"(ebias[2]), "r"(ebias[3]));
+    asm("sub.cc.u32 %0, %4, %8;\n\tsubc.cc.u32 %1, %5, %9;\n\tsubc.cc.u32 %2, %6, %10;\n\tsubc.u32 %3, %7, %11;"
+        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(w0), "r"(w1), "r"(w2), "r"(w3), "r"(s0), "r"(s1), "r"(s2), "r"(s3));
+    const bool near = frac < (1ull << 15) || frac >= (1ull << 48) - (1ull << 15);
+    Rw[0] = r0;
+    Rw[1] = r1;
+    Rw[2] = r2;
+    Rw[3] = r3;
+    near_out = near;
+    // |R| by a conditional two's-complement negation without branches
+    const uint32_t neg = r3 >> 31, msk = 0u - neg;
+    r0 ^= msk;
+    r1 ^= msk;
+    r2 ^= msk;
+    r3 ^= msk;
+    asm("add.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\taddc.u32 %3, %3, 0;"
+        : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+        : "r"(neg));
+    const uint64_t hi = ((uint64_t)r3 << 32) | r2, lo = ((uint64_t)r1 << 32) | r0;
+    const int lz = __clzll((long long)(hi | 1ull));
+    const uint64_t top = (hi << lz) | ((lo >> 1) >> (63 - lz));
+    bool sticky = (lo << lz) != 0;
+    uint64_t mant = top >> 11;
+    const uint32_t rbit = (uint32_t)(top >> 10) & 1u;
+    sticky = sticky || (top & 0x3FFull);
+    mant += rbit & (uint32_t)(sticky | (mant & 1));
+    int E2 = (128 - lz) - 53 + et + 1075;
+    const uint32_t ovf = (uint32_t)(mant >> 53);
+    mant >>= ovf;
+    E2 += (int)ovf;
+    slow = near || hi == 0 || E2 < 1 || E2 > 2046;
+    const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)(uint32_t)E2 << 52) | (mant & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
+// General finish from R = E - bias - zhat M (mod 2^128): the two-sided
+// correction when the lift was near a rounding boundary, then the correctly
+// rounded pack with gradual underflow and overflow (as kulisch_pack_fp8).
+__device__ __forceinline__ double kulisch_finish_general(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3,
+                                                         bool near, int et, const ModConsts &mc) {
+    i128 R = (i128)((((u128)r3) << 96) | (((u128)r2) << 64) | (((u128)r1) << 32) | (u128)r0);
+    if (near) {
+        const u128 M = u128_from_words(mc.M32);
+        const i128 half = (i128)u128_from_words(mc.halfM32);
+        if (R >= half) R -= (i128)M;
+        if (R < -half) R += (i128)M;
+    }
+    return pack_rne(R, et);
+}
+
 }  // namespace obfft

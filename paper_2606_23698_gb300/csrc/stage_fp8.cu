@@ -312,18 +312,89 @@ __device__ __forceinline__ void epilogue_modulus(uint32_t tacc_re, uint32_t tacc
     }
 }
 
+// Input tile of the columns [cb, cb + 128): stage 1 reads whole or partial
+// lines, one contiguous range [e0, e1) of elements; stage 2 reads K = p
+// contiguous elements per column, at addresses in arithmetic progression.
+struct InputTile {
+    int64_t e0, e1;    // stage 1: element range
+    int64_t src0, n;   // stage 2: column i starts at element src0 + i n
+    int nvalid;        // stage 2: valid columns (the first nvalid of the tile)
+};
+__device__ __forceinline__ InputTile input_tile(const ColMapT &map, int64_t ncols, int64_t cb) {
+    InputTile t;
+    if (map.stage == 1) {
+        const int64_t l0 = cb / map.p, l1 = min(cb + 127, ncols - 1) / map.p;
+        t.e0 = l0 * map.n;
+        t.e1 = (l1 + 1) * map.n;
+        t.src0 = 0;
+        t.n = 0;
+        t.nvalid = 0;
+    } else {  // a stage-2 tile lies inside one group of Lpad columns
+        const int64_t k2 = cb / map.Lpad, l0 = cb - k2 * map.Lpad;
+        t.e0 = t.e1 = 0;
+        t.src0 = l0 * map.n + k2 * map.p;
+        t.n = map.n;
+        t.nvalid = (int)max((int64_t)0, min((int64_t)128, map.L - l0));
+    }
+    return t;
+}
+// Bulk copies of the input tile into shared memory (warp-wide call), completing
+// on mbar.  Stage 2: column i goes to row i of stride (K + 1) x 16 bytes, the
+// padding keeping the 16-byte reads of a warp free of bank conflicts.
+__device__ __forceinline__ void copy_input_tile(const ColMapT &map, const InputTile &t, int K, const double2 *in,
+                                                uint8_t *sIn, uint32_t mbar, int lane) {
+    if (map.stage == 1) {
+        if (lane == 0) mbar_expect_tx(mbar, (uint32_t)((t.e1 - t.e0) * 16));
+        __syncwarp();
+        const int64_t chunk = 256;  // elements (4 KB) per copy
+        for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
+            tma_bulk_g2s(smem_u32(sIn + (e - t.e0) * 16), in + e, (uint32_t)(min(chunk, t.e1 - e) * 16), mbar);
+    } else {
+        if (lane == 0) mbar_expect_tx(mbar, (uint32_t)(t.nvalid * K * 16));
+        __syncwarp();
+        for (int i = lane; i < t.nvalid; i += 32)
+            tma_bulk_g2s(smem_u32(sIn + (int64_t)i * (K + 1) * 16), in + t.src0 + (int64_t)i * t.n,
+                         (uint32_t)(K * 16), mbar);
+    }
+}
+// L2 prefetch of an input tile (warp-wide call)
+__device__ __forceinline__ void prefetch_input_tile(const ColMapT &map, const InputTile &t, int K, const double2 *in,
+                                                    int lane) {
+    if (map.stage == 1) {
+        const int64_t chunk = 256;
+        for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + e),
+                         "r"((uint32_t)(min(chunk, t.e1 - e) * 16))
+                         : "memory");
+    } else {
+        for (int i = lane; i < t.nvalid; i += 32)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + t.src0 + (int64_t)i * t.n),
+                         "r"((uint32_t)(K * 16))
+                         : "memory");
+    }
+}
+
+// The general Kulisch finish, out of line: it runs only for the rare outputs the
+// straight-line form flags, and keeping it out of the hot code saves registers
+// and instruction cache.
+__device__ __noinline__ double kulisch_finish_slow(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, int near,
+                                                   int et) {
+    return kulisch_finish_general(r0, r1, r2, r3, near != 0, et, c_fp8_mc);
+}
+
 template <int NPAD>
 __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     stage_fp8_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab,
                      const ModConsts *__restrict__ gmc, ColMapT map, int64_t ncols, int K, int Kout,
-                     const double2 *__restrict__ in, double2 *__restrict__ out, int *status) {
+                     const double2 *__restrict__ in, double2 *__restrict__ out, int *status, int pf_ahead) {
     using CF = Fp8Cfg<NPAD>;
     constexpr int EPT = CF::EPT, OPT = CF::OPT, WPP = CF::WPP;
     constexpr int NSTEP = NMOD;  // one pipeline step per modulus
     extern __shared__ __align__(1024) uint8_t smem[];
     const ModConsts &mc = c_fp8_mc;
     __shared__ int colpart[4][128];
-    __shared__ __align__(8) uint64_t mbar[5];  // 0,1: B planes (TMA, per buffer), 2: MMA, 4: Phase-A B
+    // 0,1: B planes (TMA, per buffer), 2: MMA, 4: Phase-A B, 5: input tile
+    __shared__ __align__(8) uint64_t mbar[6];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
@@ -344,12 +415,25 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     uint8_t *sPAB = sB0 + 2 * FP8_BPLANES * planeB;
     const uint8_t *gplanes = planes + (size_t)group * FP8_PLANES_PER_GROUP * planeB;
 
+    // The input tile is copied into the front of the Phase-A staging, which the
+    // epilogues overwrite only after every thread has read its elements.
+    uint8_t *sIn = sStage;
     (void)gmc;
     if (tid < 32) reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[tid] = 0u;
     if (tid == 0) {
         abort_flag = 0;
-        for (int b = 0; b < 5; b++) mbar_init(smem_u32(&mbar[b]), 1);
+        for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
         mbar_fence_init();
+    }
+    const InputTile itile = input_tile(map, ncols, cbase);
+    if (w == 0) {
+        __syncwarp();
+        copy_input_tile(map, itile, K, in, sIn, smem_u32(&mbar[5]), lane);
+    } else if (w == 1) {
+        // the tile about one wave of CTAs ahead, most likely next on some SM
+        const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
+        if (pf_ahead > 0 && nb < (int64_t)gridDim.x)
+            prefetch_input_tile(map, input_tile(map, ncols, nb * 128), K, in, lane);
     }
     if (w == 0) tmem_alloc(smem_u32(&tmem_holder), 512);
     tc_fence_before();
@@ -392,13 +476,19 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     int64_t ibase, istride, obase, ostride;
     map.strides(cg, ibase, istride, obase, ostride);
     {
+        const bool okin = mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
+        if (!okin) atomicExch(&abort_flag, 1);
+        // element j of this column at sIn + (sbase + j sstride) * 16
+        const int64_t sbase = map.stage == 1 ? ibase - itile.e0 : (int64_t)c * (K + 1);
+        const int64_t sstride = map.stage == 1 ? istride : 1;
         uint64_t xb[EPT][2];
         int lead = LEAD_ZERO;
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
             int j = EPT * qd + jj;
             double2 x = make_double2(0.0, 0.0);
-            if (cvalid && j < K) x = in[ibase + (int64_t)j * istride];
+            if (okin && cvalid && j < K)
+                x = *reinterpret_cast<const double2 *>(sIn + (sbase + (int64_t)j * sstride) * 16);
             xb[jj][0] = (uint64_t)__double_as_longlong(x.x);
             xb[jj][1] = (uint64_t)__double_as_longlong(x.y);
             lead = max(lead, max(lead_exponent(xb[jj][0]), lead_exponent(xb[jj][1])));
@@ -483,7 +573,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     tmem_wait_st();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && abort_flag == 0) {
         tc_fence_after();
         if (!issue(0)) abort_flag = 1;
     }
@@ -522,26 +612,65 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     }
 
     // ---------------- CRT Phase A on FP16 tensor cores, then Kulisch + lift + pack ----
+    // Waves of per_wave row blocks (one block = one output k for the 128
+    // columns, N = 48 accumulators).  Accumulators start at 2^23 (the FP32 bit
+    // pattern of 2^23 + P is 0x4B000000 + P); each thread presets the next
+    // wave's columns right after reading them, so one CTA barrier per wave
+    // orders both the reads and the presets before the next wave's MMAs.
     if (ok) {
+        const int per_wave = Kout % 8 == 0 ? 8 : 10;  // 8: two row blocks per quarter-warp per wave
+        auto preset = [&](int bi) {
+            const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
+            tmem_st16_const(ta, 0x4B000000u);
+            tmem_st16_const(ta + 16, 0x4B000000u);
+            tmem_st16_const(ta + 32, 0x4B000000u);
+        };
+        for (int bi = qd; bi < min(per_wave, Kout); bi += 4) preset(bi);
+        tmem_wait_st();
+        tc_fence_before();
         fence_async_smem();
         const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
         ok = __syncthreads_or(bad) == 0;  // uniform decision across the CTA
         const uint32_t idescA = instr_desc(128, PA_N, 0);
-        const int per_wave = Kout % 8 == 0 ? 8 : 10;  // 8: two row blocks per quarter-warp per wave
         const uint32_t ebias[4] = {mc.kbias[0], mc.kbias[1], mc.kbias[2], mc.kbias[3]};
         const uint64_t zbias = ((uint64_t)mc.zbias[1] << 32) | mc.zbias[0];
+        // the 42 used accumulator words of a row block: Re 0..20, Im 24..44
+        auto load_block = [&](int bi, uint32_t (&wv)[42]) {
+            const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
+            uint32_t a[16], b[4], c16[16], d[4];
+            tmem_ld16(ta, a);
+            tmem_ld4(ta + 16, b);
+            tmem_ld1(ta + 20, wv[20]);
+            tmem_ld16(ta + 24, c16);
+            tmem_ld4(ta + 40, d);
+            tmem_ld1(ta + 44, wv[41]);
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                wv[i] = a[i];
+                wv[21 + i] = c16[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                wv[16 + i] = b[i];
+                wv[37 + i] = d[i];
+            }
+        };
+        auto after_wait = [&](uint32_t (&wv)[42]) {
+#pragma unroll
+            for (int i = 0; i < 42; i++) asm volatile("" : "+r"(wv[i]));
+        };
+        auto finish = [&](const uint32_t (&wv)[42], int kout) {
+            bool slow_re, slow_im, near_re, near_im;
+            uint32_t Rre[4], Rim[4];
+            double re = kulisch_pack_fp8_fast(wv, mc, e - 104, ebias, zbias, slow_re, Rre, near_re);
+            double im = kulisch_pack_fp8_fast(wv + 21, mc, e - 104, ebias, zbias, slow_im, Rim, near_im);
+            if (slow_re) re = kulisch_finish_slow(Rre[0], Rre[1], Rre[2], Rre[3], near_re, e - 104);
+            if (slow_im) im = kulisch_finish_slow(Rim[0], Rim[1], Rim[2], Rim[3], near_im, e - 104);
+            if (cvalid && kout < Kout) out[obase + (int64_t)kout * ostride] = make_double2(re, im);
+        };
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
             const int nb = min(per_wave, Kout - b0);
-            // accumulators start at 2^23: the FP32 bit pattern of 2^23 + P is 0x4B000000 + P
-            for (int bi = qd; bi < nb; bi += 4) {
-                const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
-                tmem_st16_const(ta, 0x4B000000u);
-                tmem_st16_const(ta + 16, 0x4B000000u);
-                tmem_st16_const(ta + 32, 0x4B000000u);
-            }
-            tmem_wait_st();
-            tc_fence_before();
-            __syncthreads();
+            const int nb_next = min(per_wave, Kout - b0 - per_wave);  // <= 0: no next wave
             if (tid == 0) {
                 tc_fence_after();
                 for (int bi = 0; bi < nb; bi++) {
@@ -558,27 +687,17 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             tc_fence_after();
             if (okm) {
                 for (int bi = qd; bi < nb; bi += 4) {
-                    const int kout = b0 + bi;
-                    uint32_t r0[16], r1[16], r2[16];
-                    const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
-                    tmem_ld16(ta, r0);
-                    tmem_ld16(ta + 16, r1);
-                    tmem_ld16(ta + 32, r2);
+                    uint32_t wv[42];
+                    load_block(bi, wv);
                     tmem_wait_ld();
-                    uint32_t words[48];
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        words[i] = r0[i];
-                        words[16 + i] = r1[i];
-                        words[32 + i] = r2[i];
-                    }
-                    const double re = kulisch_pack_fp8(words, mc, e - 104, ebias, zbias);
-                    const double im = kulisch_pack_fp8(words + 24, mc, e - 104, ebias, zbias);
-                    if (cvalid && kout < Kout) out[obase + (int64_t)kout * ostride] = make_double2(re, im);
+                    after_wait(wv);
+                    if (bi < nb_next) preset(bi);
+                    finish(wv, b0 + bi);
                 }
             } else {
                 atomicExch(&abort_flag, 1);
             }
+            tmem_wait_st();
             tc_fence_before();
             __syncthreads();
             if (abort_flag) ok = false;
@@ -586,8 +705,11 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     }
     if (!ok && tid == 0) {
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
-        // let in-flight MMAs drain (bounded) before the TMEM is freed
+        // let in-flight MMAs and copies drain (bounded) before the TMEM is freed
+        // and the CTA exits
         mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+        mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
+        mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT);
     }
     tc_fence_before();
     __syncthreads();
@@ -642,17 +764,21 @@ cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const vo
     size_t smem = fp8_smem_bytes(K, npad);
     int64_t blocks = (ncols + 127) / 128;
     if (blocks == 0) return cudaSuccess;
-    cudaError_t err;
+    int dev = 0, nsm = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
     if (npad == 16) {
         err = cudaFuncSetAttribute(stage_fp8_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         stage_fp8_kernel<16><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
-                                                                          ncols, K, K, in, out, status);
+                                                                          ncols, K, K, in, out, status, nsm);
     } else {
         err = cudaFuncSetAttribute(stage_fp8_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         stage_fp8_kernel<32><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
-                                                                          ncols, K, K, in, out, status);
+                                                                          ncols, K, K, in, out, status, nsm);
     }
     return cudaGetLastError();
 }
