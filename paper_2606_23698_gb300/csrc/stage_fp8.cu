@@ -632,6 +632,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
         ok = __syncthreads_or(bad) == 0;  // uniform decision across the CTA
         const uint32_t idescA = instr_desc(128, PA_N, 0);
+        const uint64_t adescA = smem_desc(smem_u32(sStage), 128, PA_ROWB);
+        const uint64_t bdescA0 = smem_desc(smem_u32(sPAB), 128, 512), bdescA1 = smem_desc(smem_u32(sPAB) + 256, 128, 512);
         const uint32_t ebias[4] = {mc.kbias[0], mc.kbias[1], mc.kbias[2], mc.kbias[3]};
         const uint64_t zbias = ((uint64_t)mc.zbias[1] << 32) | mc.zbias[0];
         // the 42 used accumulator words of a row block: Re 0..20, Im 24..44
@@ -673,12 +675,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             const int nb_next = min(per_wave, Kout - b0 - per_wave);  // <= 0: no next wave
             if (tid == 0) {
                 tc_fence_after();
+                // descriptors advance by the 16-byte-unit offset of the next row block
+                uint64_t ad = adescA + (uint64_t)((uint32_t)b0 * (16 * PA_ROWB / 16));
+                uint32_t d = tmem;
                 for (int bi = 0; bi < nb; bi++) {
-                    uint32_t aaddr = smem_u32(sStage) + (uint32_t)(b0 + bi) * 16 * PA_ROWB;
-                    uint32_t d = tmem + (uint32_t)(bi * PA_N);
-                    tc_mma_f16(d, smem_desc(aaddr, 128, PA_ROWB), smem_desc(smem_u32(sPAB), 128, 512), idescA, 1);
-                    tc_mma_f16(d, smem_desc(aaddr + 256, 128, PA_ROWB), smem_desc(smem_u32(sPAB) + 256, 128, 512),
-                               idescA, 1);
+                    tc_mma_f16(d, ad, bdescA0, idescA, 1);
+                    tc_mma_f16(d, ad + 16, bdescA1, idescA, 1);  // + 256 bytes: K 16..31
+                    ad += 16 * PA_ROWB / 16;
+                    d += PA_N;
                 }
                 tc_commit(smem_u32(&mbar[2]));
             }
