@@ -58,6 +58,30 @@ __device__ __forceinline__ Pieces split_pieces(int64_t xt) {
     r.p2 = (uint32_t)(v >> 40);
     return r;
 }
+// Pieces of v = x~ + 2^55 for x~ = RNE(x * 2^(52 - e)) straight from the bit
+// pattern (same value as split_pieces(scale_round(bits, e))): the significand
+// shifted right by s = e - ilogb(x) with round-half-even folded into one add,
+// q = (sig + 2^(s-1) - 1 + lsb) >> s, lsb = bit s of sig.
+__device__ __forceinline__ Pieces scale_split(uint64_t bits, int e) {
+    const uint32_t E = (uint32_t)(bits >> 52) & 0x7FFu;
+    const uint64_t sig = (bits & ((1ull << 52) - 1)) | ((uint64_t)(E != 0) << 52);
+    const int s = e + 1023 - (int)(E ? E : 1u);
+    uint64_t q;
+    if (s <= 0) {
+        q = sig << (-s);  // only when x is subnormal and leads its column
+    } else {
+        const int sc = s < 63 ? s : 63;  // sig < 2^53: any shift >= 54 rounds to 0
+        const uint64_t lsb = (sig >> sc) & 1ull;
+        q = (sig + ((1ull << (sc - 1)) - 1ull) + lsb) >> sc;
+    }
+    const uint64_t v = (bits >> 63) ? (1ull << 55) - q : (1ull << 55) + q;
+    Pieces r;
+    r.p0 = (uint32_t)v & 0xFFFFFu;
+    r.p1 = (uint32_t)(v >> 20) & 0xFFFFFu;
+    r.p2 = (uint32_t)(v >> 40);
+    return r;
+}
+
 __device__ __forceinline__ uint32_t barrett(uint32_t t, uint32_t m, uint32_t mu) {
     uint32_t q = __umulhi(t, mu);
     uint32_t r = t - q * m;

@@ -417,36 +417,44 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
 
     // The input tile is copied into the front of the Phase-A staging, which the
     // epilogues overwrite only after every thread has read its elements.
+    // Set-up runs on three warps at once: warp 0 allocates tensor memory (the
+    // slowest step), warp 1 initialises the barriers and issues the copies of
+    // the input tile and the first constants, warp 2 prefetches the input of
+    // the CTA one wave ahead into L2.
     uint8_t *sIn = sStage;
+    __shared__ int64_t s_e0;  // stage 1: first element of the input tile
     (void)gmc;
-    if (tid < 32) reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[tid] = 0u;
-    if (tid == 0) {
-        abort_flag = 0;
-        for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
-        mbar_fence_init();
-    }
-    const InputTile itile = input_tile(map, ncols, cbase);
     if (w == 0) {
+        tmem_alloc(smem_u32(&tmem_holder), 512);
+    } else if (w == 1) {
+        const InputTile itile = input_tile(map, ncols, cbase);
+        if (lane == 0) {
+            abort_flag = 0;
+            s_e0 = itile.e0;
+            for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
+            mbar_fence_init();
+        }
         __syncwarp();
         copy_input_tile(map, itile, K, in, sIn, smem_u32(&mbar[5]), lane);
-    } else if (w == 1) {
+        if (lane == 0) {
+            mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
+            tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
+            const uint32_t bytes0 = 4 * fp8_ndig(0) * planeB;
+            mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
+            tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
+        }
+    } else if (w == 2) {
         // the tile about one wave of CTAs ahead, most likely next on some SM
         const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
         if (pf_ahead > 0 && nb < (int64_t)gridDim.x)
             prefetch_input_tile(map, input_tile(map, ncols, nb * 128), K, in, lane);
+    } else if (w == 3) {
+        reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[lane] = 0u;
     }
-    if (w == 0) tmem_alloc(smem_u32(&tmem_holder), 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
-    if (tid == 0) {
-        mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
-        tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
-        const uint32_t bytes0 = 4 * fp8_ndig(0) * planeB;
-        mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
-        tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
-    }
     // classes 2..4 start at zero (issue_modulus_nm)
 #pragma unroll
     for (int cl = 2; cl < 5; cl++)
@@ -479,7 +487,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const bool okin = mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
         if (!okin) atomicExch(&abort_flag, 1);
         // element j of this column at sIn + (sbase + j sstride) * 16
-        const int64_t sbase = map.stage == 1 ? ibase - itile.e0 : (int64_t)c * (K + 1);
+        const int64_t sbase = map.stage == 1 ? ibase - s_e0 : (int64_t)c * (K + 1);
         const int64_t sstride = map.stage == 1 ? istride : 1;
         uint64_t xb[EPT][2];
         int lead = LEAD_ZERO;
@@ -499,8 +507,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         e = l2 == LEAD_ZERO ? 0 : l2;
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
-            pR[jj] = split_pieces(scale_round(xb[jj][0], e));
-            pI[jj] = split_pieces(scale_round(xb[jj][1], e));
+            pR[jj] = scale_split(xb[jj][0], e);
+            pI[jj] = scale_split(xb[jj][1], e);
         }
     }
 
@@ -617,6 +625,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // pattern of 2^23 + P is 0x4B000000 + P); each thread presets the next
     // wave's columns right after reading them, so one CTA barrier per wave
     // orders both the reads and the presets before the next wave's MMAs.
+    uint32_t mph3 = 0u;   // next phase parity of mbar[3] (second commit group of a Phase-A wave)
+    bool pend3 = false;   // a commit to mbar[3] is in flight (thread 0's view)
     if (ok) {
         const int per_wave = Kout % 8 == 0 ? 8 : 10;  // 8: two row blocks per quarter-warp per wave
         auto preset = [&](int bi) {
@@ -673,34 +683,44 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
             const int nb = min(per_wave, Kout - b0);
             const int nb_next = min(per_wave, Kout - b0 - per_wave);  // <= 0: no next wave
+            // two commits per wave: row blocks 0..3 on mbar[2], the rest (possibly
+            // none) on mbar[3], so the second group's MMAs run while the first
+            // group is finished; every thread waits once on each barrier per wave
             if (tid == 0) {
                 tc_fence_after();
                 // descriptors advance by the 16-byte-unit offset of the next row block
                 uint64_t ad = adescA + (uint64_t)((uint32_t)b0 * (16 * PA_ROWB / 16));
                 uint32_t d = tmem;
+                const int na = min(nb, 4);
                 for (int bi = 0; bi < nb; bi++) {
                     tc_mma_f16(d, ad, bdescA0, idescA, 1);
                     tc_mma_f16(d, ad + 16, bdescA1, idescA, 1);  // + 256 bytes: K 16..31
                     ad += 16 * PA_ROWB / 16;
                     d += PA_N;
+                    if (bi == na - 1) tc_commit(smem_u32(&mbar[2]));
                 }
-                tc_commit(smem_u32(&mbar[2]));
+                tc_commit(smem_u32(&mbar[3]));
+                pend3 = true;
             }
-            bool okm = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+            auto do_block = [&](int bi) {
+                uint32_t wv[42];
+                load_block(bi, wv);
+                tmem_wait_ld();
+                after_wait(wv);
+                if (bi < nb_next) preset(bi);
+                finish(wv, b0 + bi);
+            };
+            const bool okA = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
             mph[0] ^= 1u;
             tc_fence_after();
-            if (okm) {
-                for (int bi = qd; bi < nb; bi += 4) {
-                    uint32_t wv[42];
-                    load_block(bi, wv);
-                    tmem_wait_ld();
-                    after_wait(wv);
-                    if (bi < nb_next) preset(bi);
-                    finish(wv, b0 + bi);
-                }
-            } else {
-                atomicExch(&abort_flag, 1);
-            }
+            if (okA && qd < nb) do_block(qd);
+            const bool okB = mbar_wait(smem_u32(&mbar[3]), mph3, WAIT_LIMIT);
+            mph3 ^= 1u;
+            pend3 = false;
+            tc_fence_after();
+            if (okA && okB)
+                for (int bi = qd + 4; bi < nb; bi += 4) do_block(bi);
+            if (!(okA && okB)) atomicExch(&abort_flag, 1);
             tmem_wait_st();
             tc_fence_before();
             __syncthreads();
@@ -712,6 +732,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         // let in-flight MMAs and copies drain (bounded) before the TMEM is freed
         // and the CTA exits
         mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+        if (pend3) mbar_wait(smem_u32(&mbar[3]), mph3, WAIT_LIMIT);
         mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
         mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT);
     }
