@@ -556,14 +556,16 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // buffer of modulus k-1, whose MMAs have completed.
     const uint64_t bdesc0 = smem_desc(smem_u32(sB0), 128, 256);
     const uint64_t bdesc1 = smem_desc(smem_u32(sB0 + FP8_BPLANES * planeB), 128, 256);
+    // Copy of the constant planes of modulus k into B buffer k & 1, whose
+    // previous contents (modulus k - 2) are no longer read by any MMA.
+    auto prefetch_b = [&](int k) {
+        const uint32_t bytes = 4 * fp8_ndig(k) * planeB;
+        mbar_expect_tx(smem_u32(&mbar[k & 1]), bytes);
+        tma_bulk_g2s(smem_u32(sB0 + (k & 1) * FP8_BPLANES * planeB), gplanes + (size_t)fp8_plane_offset(k) * planeB,
+                     bytes, smem_u32(&mbar[k & 1]));
+    };
     auto issue = [&](int k) -> bool {
         if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
-        if (k + 1 < NMOD) {
-            const uint32_t bytes = 4 * fp8_ndig(k + 1) * planeB;
-            mbar_expect_tx(smem_u32(&mbar[(k + 1) & 1]), bytes);
-            tma_bulk_g2s(smem_u32(sB0 + ((k + 1) & 1) * FP8_BPLANES * planeB),
-                         gplanes + (size_t)fp8_plane_offset(k + 1) * planeB, bytes, smem_u32(&mbar[(k + 1) & 1]));
-        }
         const uint64_t bd = (k & 1) ? bdesc1 : bdesc0;
         const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * APL_COLS;
         const int kind = fp8_kind(k);
@@ -584,6 +586,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     if (tid == 0 && abort_flag == 0) {
         tc_fence_after();
         if (!issue(0)) abort_flag = 1;
+    } else if (tid == 32 && NMOD > 1) {
+        prefetch_b(1);  // buffer 1 is unused so far
     }
     __syncthreads();
     bool ok = abort_flag == 0;
@@ -612,9 +616,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             ok = false;
             break;
         }
+        // MMAs of modulus k+1 from thread 0; the constant planes of modulus k+2
+        // from another warp, into the buffer of modulus k (its MMAs completed:
+        // every thread waited for them before this barrier)
         if (tid == 0 && k + 1 < NSTEP) {
             tc_fence_after();
             if (!issue(k + 1)) abort_flag = 1;
+        } else if (tid == 32 && k + 2 < NSTEP) {
+            prefetch_b(k + 2);
         }
         // an abort raised by issue() is seen after the next step's barrier
     }
