@@ -330,24 +330,26 @@ def main():
     # e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
     if not args.no_e2e:
+        # the public host-to-host call: the 16 GiB input and output copies run
+        # inside it, overlapped with the first and last axis passes
         hx = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
         hx.copy_(x)
         hy = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-        dx = torch.empty_like(x)
+        pl.exec_host(hx, hy, stream=stream)  # warm-up: allocates the plan's staging buffers
+        torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         esteps = max(1, min(args.steps, 2))
         e0.record(stream)
         for _ in range(esteps):
-            dx.copy_(hx, non_blocking=True)
-            pl.exec(dx, y)
-            hy.copy_(y, non_blocking=True)
+            pl.exec_host(hx, hy, stream=stream)
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1) / esteps
         nbytes = x.numel() * 16
-        e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
-        del hx, hy, dx
+        e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "call": "obfft_exec_host"}
+        del hx, hy
 
     extra = None
     if not args.no_extra and rank == 0 and n == 1024:

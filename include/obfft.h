@@ -121,6 +121,26 @@ obfft_status obfft_exec_stage(obfft_plan p, int axis, int stage, const void *in,
                               void *stream);
 
 /*
+ * Transform from host memory to host memory (one-grid plans): in and out are
+ * host pointers to batch * n0 * n1 * n2 complex128 values in the layout of
+ * obfft_exec (page-locked memory makes the copies asynchronous; pageable
+ * memory works, with copies that block the host thread).  Not part of the
+ * paper: the copies are overlapped with the transform.  The input is copied in
+ * chunks of lines of the first axis pass (axis 2), each chunk transformed as
+ * soon as it has arrived; the last pass (axis 0) runs in chunks of lines and
+ * each chunk's output is copied back while the next one computes.  The plan
+ * allocates two device buffers of the grid's size on the first call and keeps
+ * them, with an internal copy stream and events, until obfft_destroy.  Work is
+ * ordered after prior work on `stream` (a cudaStream_t, NULL = legacy default)
+ * and the host output is complete once `stream` reaches the point after the
+ * call.  Calls on one plan must not overlap in time on different streams
+ * (they share the device buffers).  Errors: OBFFT_ERR_ARG (NULL pointers,
+ * in == out, overlapping ranges, multi-grid plan, bad dir), OBFFT_ERR_ALLOC,
+ * OBFFT_ERR_CUDA.
+ */
+obfft_status obfft_exec_host(obfft_plan p, const void *in, void *out, int dir, void *stream);
+
+/*
  * Device status of the plan: synchronises `stream` (a cudaStream_t), reads the
  * plan's status word and returns OBFFT_ERR_TIMEOUT if a kernel's bounded wait
  * on a tensor-core completion or a TMA copy gave up since the last call (the

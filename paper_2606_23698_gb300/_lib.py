@@ -30,7 +30,8 @@ MODES = {"fp8": OBFFT_MODE_FP8, "int8": OBFFT_MODE_INT8, "fp64": OBFFT_MODE_FP64
 EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_splits",
            "obfft_plan_create_many", "obfft_exec_many", "obfft_exec_stage", "obfft_last_error",
            "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants",
-           "obfft_exec_fp64_noalloc", "obfft_plan_status", "obfft_selftest_bounded_wait")
+           "obfft_exec_fp64_noalloc", "obfft_plan_status", "obfft_selftest_bounded_wait",
+           "obfft_exec_host")
 
 _lib = None
 
@@ -53,11 +54,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, i64, i64, i32]
     L.obfft_plan_create_many.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i64), i32]
     L.obfft_exec.argtypes = [vp, vp, vp, i32, vp]
+    L.obfft_exec_host.argtypes = [vp, vp, vp, i32, vp]
     L.obfft_exec_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp]
     L.obfft_exec_stage.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     L.obfft_destroy.argtypes = [vp]
     L.obfft_plan_get_splits.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
-    for f in ("obfft_plan_create", "obfft_plan_create_many", "obfft_exec", "obfft_exec_many",
+    for f in ("obfft_plan_create", "obfft_plan_create_many", "obfft_exec", "obfft_exec_host", "obfft_exec_many",
               "obfft_exec_stage", "obfft_destroy", "obfft_plan_get_splits"):
         getattr(L, f).restype = i32
     L.obfft_last_error.restype = ctypes.c_char_p
@@ -100,6 +102,10 @@ def obfft_plan_create_many(dims, mode: int = OBFFT_MODE_FP8) -> int:
 
 def obfft_exec(plan: int, in_ptr: int, out_ptr: int, dir: int, stream: int = 0) -> None:
     check(load().obfft_exec(plan, in_ptr, out_ptr, dir, stream))
+
+
+def obfft_exec_host(plan: int, in_ptr: int, out_ptr: int, dir: int, stream: int = 0) -> None:
+    check(load().obfft_exec_host(plan, in_ptr, out_ptr, dir, stream))
 
 
 def obfft_exec_many(plan: int, in_ptrs, out_ptrs, dir: int, stream: int = 0) -> None:

@@ -1,7 +1,9 @@
 """torch-tensor layer over the C ABI: plans as objects, tensors as pointers.
 
-Only argument marshalling: the transform itself runs in libobfft.so.  Inputs
-must be contiguous complex128 CUDA tensors; no host or CPU path exists.
+Only argument marshalling: the transform itself runs in libobfft.so, on the
+GPU.  exec / exec_stage take contiguous complex128 CUDA tensors; exec_host takes
+host tensors, which the library copies to and from the GPU around (and
+overlapped with) the same GPU transform.  No CPU compute path exists.
 """
 from __future__ import annotations
 
@@ -52,6 +54,23 @@ class Plan:
         _check_tensor(out, self.numel, "output")
         s = stream if stream is not None else torch.cuda.current_stream(x.device)
         _lib.obfft_exec(self.handle, x.data_ptr(), out.data_ptr(), dir, s.cuda_stream)
+        return out
+
+    def exec_host(self, x: torch.Tensor, out: torch.Tensor | None = None, dir: int = -1,
+                  stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+        """Host-to-host transform (obfft_exec_host): x and out are contiguous
+        complex128 CPU tensors, ideally pinned; the copies overlap the transform.
+        The output is complete once `stream` (default: current) is synchronised."""
+        if x.device.type != "cpu" or x.dtype != torch.complex128 or not x.is_contiguous() \
+                or x.numel() != self.numel:
+            raise ValueError(f"input must be a contiguous complex128 CPU tensor of {self.numel} elements")
+        if out is None:
+            out = torch.empty(x.shape, dtype=x.dtype, pin_memory=x.is_pinned())
+        if out.device.type != "cpu" or out.dtype != torch.complex128 or not out.is_contiguous() \
+                or out.numel() != self.numel:
+            raise ValueError(f"output must be a contiguous complex128 CPU tensor of {self.numel} elements")
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _lib.obfft_exec_host(self.handle, x.data_ptr(), out.data_ptr(), dir, s.cuda_stream)
         return out
 
     def exec_stage(self, axis: int, stage: int, x: torch.Tensor, out: torch.Tensor, dir: int = -1):

@@ -108,6 +108,11 @@ struct obfft_plan_s {
     std::vector<void *> graph_outs;
     int graph_dir = 0;
     std::vector<void *> grid_scratch;  // scratch of grid g (offsets into `scratch`)
+    // host-to-host execution: two grid-sized device buffers, a copy stream and
+    // its events, created on the first obfft_exec_host call
+    void *host_io[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
 };
 
 namespace obfft {

@@ -15,6 +15,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -674,6 +675,10 @@ extern "C" obfft_status obfft_destroy(obfft_plan p) {
     free_tables(p);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+    if (p->copy_stream) cudaStreamSynchronize(p->copy_stream), cudaStreamDestroy(p->copy_stream);
+    for (cudaEvent_t ev : p->copy_events) cudaEventDestroy(ev);
+    cudaFree(p->host_io[0]);
+    cudaFree(p->host_io[1]);
     cudaFree(p->scratch);
     cudaFree(p->d_consts);
     cudaFree(p->d_pab);
@@ -702,12 +707,10 @@ static StageGeom pass_geom(const GridDesc &gd, int64_t batch, int axis) {
     return g;
 }
 
-static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, int axis, int stage,
-                              const double2 *in, double2 *out, int dir, cudaStream_t s) {
-    const AxisPlan &ap = gd.ax[axis];
+static obfft_status run_stage_geom(obfft_plan P, const AxisPlan &ap, const StageGeom &g, int stage,
+                                   const double2 *in, double2 *out, int dir, cudaStream_t s) {
     AxisTables *t = get_tables(P, ap.n, ap.p, ap.q, dir);
     if (!t) return set_error(OBFFT_ERR_INTERNAL, "missing tables");
-    StageGeom g = pass_geom(gd, batch, axis);
     cudaError_t e;
     if (P->mode == OBFFT_MODE_INT8)
         e = launch_stage_int8(*t, P->d_consts, g, stage, in, out, s);
@@ -719,6 +722,11 @@ static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, i
         return set_error(OBFFT_ERR_ARG, "mode not available in this build");
     if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return OBFFT_OK;
+}
+
+static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, int axis, int stage,
+                              const double2 *in, double2 *out, int dir, cudaStream_t s) {
+    return run_stage_geom(P, gd.ax[axis], pass_geom(gd, batch, axis), stage, in, out, dir, s);
 }
 
 static obfft_status exec_grid(obfft_plan P, const GridDesc &gd, int64_t batch, const double2 *in,
@@ -766,6 +774,142 @@ extern "C" obfft_status obfft_exec(obfft_plan p, const void *in, void *out, int 
     uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
     if (a < b + bytes && b < a + bytes) return set_error(OBFFT_ERR_ARG, "in and out overlap");
     return exec_grid(p, p->grids[0], p->batch, (const double2 *)in, (double2 *)out, dir, (cudaStream_t)stream);
+}
+
+// Host-to-host execution of a one-grid plan with the copies overlapped: the
+// input arrives in chunks of lines of the first pass (axis 2), each chunk is
+// transformed as soon as it has landed; the last pass (axis 0) runs in chunks
+// of lines and each chunk's output (n0 runs of the chunk's lines, pitch P) is
+// copied back while the next chunk computes.  A chunk lies inside one batch
+// item, so the stage kernels address its output with the item's full line
+// count P from pointers offset to the chunk.
+static obfft_status cuda_err(cudaError_t e, const char *what) {
+    return e == cudaSuccess ? OBFFT_OK : set_error(OBFFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" obfft_status obfft_exec_host(obfft_plan p, const void *host_in, void *host_out, int dir, void *stream) {
+    if (!p) return set_error(OBFFT_ERR_ARG, "plan is NULL");
+    if (dir != -1 && dir != 1) return set_error(OBFFT_ERR_ARG, "dir must be -1 or +1");
+    if (!host_in || !host_out) return set_error(OBFFT_ERR_ARG, "host_in/host_out is NULL");
+    if (host_in == host_out) return set_error(OBFFT_ERR_ARG, "host_in == host_out: out-of-place only");
+    if (p->grids.size() != 1) return set_error(OBFFT_ERR_ARG, "plan has several grids: one grid only");
+    const GridDesc &gd = p->grids[0];
+    const int64_t B = p->batch;
+    const int64_t total = gd.n[0] * gd.n[1] * gd.n[2] * B;
+    const size_t bytes = (size_t)total * 16;
+    {
+        uintptr_t a = (uintptr_t)host_in, b = (uintptr_t)host_out;
+        if (a < b + bytes && b < a + bytes) return set_error(OBFFT_ERR_ARG, "host_in and host_out overlap");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const char *hin = (const char *)host_in;
+    char *hout = (char *)host_out;
+    for (int i = 0; i < 2; i++)
+        if (!p->host_io[i]) {
+            cudaError_t e = cudaMalloc(&p->host_io[i], bytes);
+            if (e != cudaSuccess) return set_error(OBFFT_ERR_ALLOC, std::string("host staging: ") + cudaGetErrorString(e));
+        }
+    double2 *d0 = (double2 *)p->host_io[0], *d1 = (double2 *)p->host_io[1];
+    double2 *scr = (double2 *)p->scratch;
+    // chunks: up to 8 per batch item, never fewer than 2^20 elements each
+    const int64_t n2 = gd.ax[2].n, n0 = gd.ax[0].n;
+    const int64_t P2 = gd.n[0] * gd.n[1], P0 = gd.n[1] * gd.n[2];
+    auto nchunks = [](int64_t lines, int64_t len) {
+        int64_t c = std::min<int64_t>(8, std::max<int64_t>(1, lines * len / ((int64_t)1 << 20)));
+        return (int)std::min<int64_t>(c, lines);
+    };
+    const int c2 = nchunks(P2, n2), c0 = nchunks(P0, n0);
+    const bool simple = gd.ax[2].n == 1 || gd.ax[0].n == 1 || (c2 == 1 && c0 == 1 && B == 1);
+    obfft_status st;
+    if (simple) {
+        st = cuda_err(cudaMemcpyAsync(d0, hin, bytes, cudaMemcpyHostToDevice, s), "input copy");
+        if (st != OBFFT_OK) return st;
+        st = exec_grid(p, gd, B, d0, d1, dir, s);
+        if (st != OBFFT_OK) return st;
+        return cuda_err(cudaMemcpyAsync(hout, d1, bytes, cudaMemcpyDeviceToHost, s), "output copy");
+    }
+    if (!p->copy_stream) {
+        st = cuda_err(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "copy stream");
+        if (st != OBFFT_OK) return st;
+    }
+    const size_t nev = (size_t)B * (c2 + c0) + 2;
+    while (p->copy_events.size() < nev) {
+        cudaEvent_t ev;
+        st = cuda_err(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+        if (st != OBFFT_OK) return st;
+        p->copy_events.push_back(ev);
+    }
+    size_t ei = 0;
+    cudaEvent_t start = p->copy_events[ei++];
+    st = cuda_err(cudaEventRecord(start, s), "event record");
+    if (st == OBFFT_OK) st = cuda_err(cudaStreamWaitEvent(p->copy_stream, start, 0), "stream wait");
+    if (st != OBFFT_OK) return st;
+    auto chunk = [](int64_t lines, int c, int i, int64_t *r0, int64_t *lc) {
+        const int64_t per = (lines + c - 1) / c;
+        *r0 = per * i;
+        *lc = std::min(per, lines - *r0);
+    };
+    // pass 1 (axis 2): input copies on the copy stream, stages on `s` per chunk
+    const AxisPlan &a2 = gd.ax[2];
+    for (int64_t b = 0; b < B; b++)
+        for (int i = 0; i < c2; i++) {
+            int64_t r0, lc;
+            chunk(P2, c2, i, &r0, &lc);
+            if (lc <= 0) continue;
+            const int64_t off = (b * P2 + r0) * n2;
+            cudaEvent_t ev = p->copy_events[ei++];
+            st = cuda_err(cudaMemcpyAsync(d0 + off, hin + off * 16, (size_t)lc * n2 * 16, cudaMemcpyHostToDevice,
+                                          p->copy_stream), "input copy");
+            if (st == OBFFT_OK) st = cuda_err(cudaEventRecord(ev, p->copy_stream), "event record");
+            if (st == OBFFT_OK) st = cuda_err(cudaStreamWaitEvent(s, ev, 0), "stream wait");
+            if (st != OBFFT_OK) return st;
+            StageGeom g;
+            g.L = lc;
+            g.P = P2;
+            g.n = a2.n; g.p = a2.p; g.q = a2.q;
+            st = run_stage_geom(p, a2, g, 1, d0 + off, scr + off, dir, s);
+            if (st == OBFFT_OK) st = run_stage_geom(p, a2, g, 2, scr + off, d1 + b * n2 * P2 + r0, dir, s);
+            if (st != OBFFT_OK) return st;
+        }
+    // pass 2 (axis 1), on the device only
+    if (gd.ax[1].n == 1) {
+        st = cuda_err(cudaMemcpyAsync(d0, d1, bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    } else {
+        st = run_stage(p, gd, B, 1, 1, d1, scr, dir, s);
+        if (st == OBFFT_OK) st = run_stage(p, gd, B, 1, 2, scr, d0, dir, s);
+    }
+    if (st != OBFFT_OK) return st;
+    // pass 3 (axis 0): stages per chunk on `s`, output copies on the copy stream
+    const AxisPlan &a0 = gd.ax[0];
+    for (int64_t b = 0; b < B; b++)
+        for (int i = 0; i < c0; i++) {
+            int64_t r0, lc;
+            chunk(P0, c0, i, &r0, &lc);
+            if (lc <= 0) continue;
+            const int64_t off = (b * P0 + r0) * n0;
+            StageGeom g;
+            g.L = lc;
+            g.P = P0;
+            g.n = a0.n; g.p = a0.p; g.q = a0.q;
+            const int64_t ooff = b * n0 * P0 + r0;
+            st = run_stage_geom(p, a0, g, 1, d0 + off, scr + off, dir, s);
+            if (st == OBFFT_OK) st = run_stage_geom(p, a0, g, 2, scr + off, d1 + ooff, dir, s);
+            if (st != OBFFT_OK) return st;
+            cudaEvent_t ev = p->copy_events[ei++];
+            st = cuda_err(cudaEventRecord(ev, s), "event record");
+            if (st == OBFFT_OK) st = cuda_err(cudaStreamWaitEvent(p->copy_stream, ev, 0), "stream wait");
+            if (st == OBFFT_OK)
+                st = cuda_err(cudaMemcpy2DAsync(hout + ooff * 16, (size_t)P0 * 16, d1 + ooff, (size_t)P0 * 16,
+                                                (size_t)lc * 16, (size_t)n0, cudaMemcpyDeviceToHost, p->copy_stream),
+                              "output copy");
+            if (st != OBFFT_OK) return st;
+        }
+    // the caller's stream completes after the last output copy
+    cudaEvent_t done = p->copy_events[ei++];
+    st = cuda_err(cudaEventRecord(done, p->copy_stream), "event record");
+    if (st == OBFFT_OK) st = cuda_err(cudaStreamWaitEvent(s, done, 0), "stream wait");
+    if (st != OBFFT_OK) return st;
+    return cuda_err(cudaGetLastError(), "launch");
 }
 
 // Multi-grid execution (the uneven batch).  Every grid gets its own slice of

@@ -216,3 +216,43 @@ def test_device_timeout_reported_without_fault():
     x = S.complex_uniform(1, (8, 8, 8)).numpy()
     y = run(pl, x)                                          # still works
     assert bits_equal(y, oracle_full(x, splits_of(pl), -1))
+
+
+@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("shape,batch", [((96, 160, 144), 1), ((64, 48, 128), 2), ((8, 8, 8), 1)])
+def test_exec_host_matches_device_exec(mode, shape, batch):
+    """obfft_exec_host (chunked copies overlapped with the first and last axis
+    passes, and the plain path for small grids) gives the device transform's
+    result bit for bit, forward and inverse, on two calls in a row."""
+    x = S.complex_uniform(S.SEED_UNEVEN, (batch,) + shape)
+    pl = plan(shape, mode, batch=batch)
+    xd = x.cuda()
+    hx = x.pin_memory()
+    for d in (-1, 1):
+        ref_ = pl.exec(xd, dir=d)
+        torch.cuda.synchronize()
+        ref_ = ref_.cpu()
+        for _ in range(2):
+            hy = torch.full_like(hx, complex(float("nan"), 0.0)).pin_memory()
+            pl.exec_host(hx, hy, dir=d)
+            torch.cuda.synchronize()
+            assert torch.equal(hy.view(torch.int64), ref_.view(torch.int64))
+    # pageable host memory takes the same path with blocking copies
+    hy = torch.empty_like(x)
+    pl.exec_host(x, hy)
+    torch.cuda.synchronize()
+    assert torch.equal(hy.view(torch.int64), pl.exec(xd).cpu().view(torch.int64))
+
+
+def test_exec_host_argument_errors():
+    from paper_2606_23698_gb300 import ObfftError, _lib
+    pl = plan((8, 8, 8), "fp8")
+    x = torch.zeros(512, dtype=torch.complex128)
+    with pytest.raises(ObfftError):
+        _lib.obfft_exec_host(pl.handle, 0, x.data_ptr(), -1, 0)
+    with pytest.raises(ObfftError):
+        _lib.obfft_exec_host(pl.handle, x.data_ptr(), x.data_ptr(), -1, 0)
+    with pytest.raises(ObfftError):
+        _lib.obfft_exec_host(pl.handle, x.data_ptr(), x.data_ptr() + 16, -1, 0)  # overlap
+    with pytest.raises(ValueError):
+        pl.exec_host(x.cuda())
