@@ -372,11 +372,17 @@ def main():
     alg_inst = 2 * c_epi * N3  # per stage launch: 2 scalar outputs per complex element
     achieved = alg_inst / (kern_ms * 1e-3) / 1e12
     hbm_bytes = 32 * N3  # per stage launch: 16 B read + 16 B written per element
-    # tensor ops per stage launch (MAC = 2): FP8 mode issues 171 K=32 E4M3 MMAs per
-    # 4096 complex outputs (M=128 x N=32) plus Phase A (K=32 padded x N=48 FP16)
-    fp8_ops = 2 * N3 * (171 * 32 + 32 * 48)
+    # tensor ops per stage launch (MAC = 2): the real-form complex product takes
+    # 228 E4M3 digit products of K = 32 per complex output (4 real products x 57),
+    # plus Phase A (K = 32 padded x N = 48 FP16)
+    fp8_ops = 2 * N3 * (228 * 32 + 32 * 48)
+    # DRAM bytes per FP8 stage launch at 1024^3 from one ncu capture of the same
+    # kernel on a 16 x 1024 x 1024 grid (256 MiB in and out, above L2):
+    # dram__bytes_read.sum 268,664,320 + dram__bytes_write.sum 222,497,536,
+    # scaled by the 64 times more columns of a 1024^3 launch
+    traffic = (268664320 + 222497536) * 64 if (mode == "fp8" and n == 1024) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinst/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak, "traffic": traffic,
                 "kernel": f"stage_{mode}_kernel (axis 2, stage 1)", "kernel_ms": kern_ms,
                 "algorithmic": f"{2 * c_epi} integer instructions per complex output (paper c_epi = {c_epi} per scalar)",
                 "peak_note": "derived: 152 SMs x 4 schedulers x 32 lanes x max SM clock",
