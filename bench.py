@@ -33,7 +33,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default=None, help="fp8 | int8 (headline Ozaki mode)")
+    ap.add_argument("--mode", default=None, help="fp8 | int8 | fp16 (headline Ozaki mode)")
     ap.add_argument("--size", type=int, default=1024, help="cube edge (debug only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -171,7 +171,7 @@ def side_configs(torch, Plan, PlanMany, S, mode):
     x = S.complex_wide_range(S.SEED_256_WIDE, (n, n, n), device="cuda")
     y64 = Plan(n, n, n, mode="fp64").exec(x, dir=-1)
     res = {}
-    for m in ("fp8", "int8", "fp64"):
+    for m in ("fp8", "int8", "fp16", "fp64"):
         pl = Plan(n, n, n, mode=m)
         y = pl.exec(x, dir=-1)
         torch.cuda.synchronize()
@@ -315,7 +315,7 @@ def main():
 
     # comparator modes at the same size
     modes = {mode: ms_step}
-    others = [m for m in ("fp8", "int8", "fp64") if m != mode]
+    others = [m for m in ("fp8", "int8", "fp16", "fp64") if m != mode]
     for m in others:
         pl2, ms2 = time_mode(m, max(1, min(args.steps, 2)), 1)
         modes[m] = ms2 / max(1, min(args.steps, 2))

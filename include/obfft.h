@@ -54,7 +54,11 @@ typedef enum {
        (the INT8 kind sm_103a accepts), two-limb residues */
     OBFFT_MODE_INT8 = 1,
     /* comparator: plain FP64 six-step FFT (radix butterflies + FP64 twiddles) */
-    OBFFT_MODE_FP64_NATIVE = 2
+    OBFFT_MODE_FP64_NATIVE = 2,
+    /* residue GEMMs on tcgen05 FP16 tensor cores (kind::f16), the FP16-carrier
+       variant: each balanced data residue is one FP16 operand (no digit split),
+       each constant residue two FP16 digits c0 + 32 c1; Phase A as in FP8 mode */
+    OBFFT_MODE_FP16 = 3
 } obfft_mode;
 
 /*

@@ -117,6 +117,33 @@ def check_fp8_layout(m: int, K: int = 32) -> dict:
             "classes": len(pairs), "max_digit": maxd, "max_combined": int(comb_max)}
 
 
+def check_fp16_carrier(m: int, K: int = 64) -> dict:
+    """FP16-carrier layout: every balanced data residue v is one FP16 operand;
+    every balanced constant residue a = c0 + 32 c1 with c1 = RNE(a / 32).
+    Checks, for every residue of m: both digits and v are FP16-exact integers,
+    c0 + 32 c1 = a, and over K terms (both halves of the real-form complex
+    product, K = 64) the c0-class stays below 2^24 and the c1-class below 2^22
+    (so its reduction mod m by one rounded FP32 quotient is exact), and the
+    class-0 sum plus 32 times the reduced class-1 stays below 2^24."""
+    a = balanced(m)
+    c1 = rne_div(a, 32)
+    c0 = a - 32 * c1
+    assert np.array_equal(c0 + 32 * c1, a), m
+    assert np.abs(c0).max() <= 16 and np.abs(c1).max() <= 32, m
+    vmax = int(np.abs(a).max())  # data residues share the balanced range
+    assert vmax <= 2048  # FP16 represents every integer up to 2048
+    cls0 = K * int(np.abs(c0).max()) * vmax
+    cls1 = K * int(np.abs(c1).max()) * vmax
+    assert cls0 < 2 ** 24 and cls1 < 2 ** 22, (m, cls0, cls1)
+    comb = cls0 + 32 * (m // 2 + 1)
+    assert comb < 2 ** 24
+    # the recombination is exact integer algebra: c0 v + 32 (c1 v) = a v
+    v = a[:, None]
+    assert np.array_equal(c0[None, :] * v + 32 * (c1[None, :] * v), a[None, :] * v)
+    return {"modulus": m, "max_c0": int(np.abs(c0).max()), "max_c1": int(np.abs(c1).max()),
+            "class0_max": cls0, "class1_max": cls1}
+
+
 def check_int8_two_limb(m: int) -> None:
     """v = v0 + 256 v1 with v0 in [-128, 128), v1 in [0, 8] for every canonical residue."""
     v = np.arange(m, dtype=np.int64)

@@ -24,7 +24,9 @@ STATUS_NAMES = {0: "OBFFT_OK", 1: "OBFFT_ERR_ARG", 2: "OBFFT_ERR_UNSUPPORTED_SIZ
 OBFFT_MODE_FP8 = 0
 OBFFT_MODE_INT8 = 1
 OBFFT_MODE_FP64_NATIVE = 2
-MODES = {"fp8": OBFFT_MODE_FP8, "int8": OBFFT_MODE_INT8, "fp64": OBFFT_MODE_FP64_NATIVE}
+OBFFT_MODE_FP16 = 3
+MODES = {"fp8": OBFFT_MODE_FP8, "int8": OBFFT_MODE_INT8, "fp64": OBFFT_MODE_FP64_NATIVE,
+         "fp16": OBFFT_MODE_FP16}
 
 # every symbol include/obfft.h declares
 EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_splits",

@@ -28,6 +28,8 @@ constexpr int RES_OFFSET = 1024;
 // digit (x_R half: a_R, a_I; x_I half: -a_I, a_R), 3 digits for the three
 // 11-bit moduli and 2 for the other nine.
 constexpr int FP8_PLANES_PER_GROUP = 4 * (3 * 3 + 9 * 2);
+// FP16-carrier mode: per modulus 8 planes (2 halves x 2 constant digits x Re/Im rows)
+constexpr int FP16_PLANES_PER_GROUP = 8 * 12;
 
 struct ModConsts {
     uint32_t m[NMOD];         // moduli
@@ -131,6 +133,9 @@ cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const S
                               int stage, const double2 *in, double2 *out, cudaStream_t s);
 cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
+cudaError_t launch_stage_fp16(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
+                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
+std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups, int K);
 size_t fp8_smem_bytes(int Kout, int npad);
 cudaError_t fp8_upload_constants();  // once per device, outside any stream capture
 cudaError_t launch_bounded_wait_selftest(int *status, cudaStream_t s);

@@ -263,6 +263,9 @@ static uint16_t f16_of_small(int v) {  // exact for 0 <= v < 2048
     int mant = ((v << 10) >> e) & 0x3FF;
     return (uint16_t)(((e + 15) << 10) | mant);
 }
+static uint16_t f16_of_small_int(int v) {  // exact for |v| < 2048
+    return v < 0 ? (uint16_t)(0x8000u | f16_of_small(-v)) : f16_of_small(v);
+}
 static int64_t rne_div(int64_t v, int64_t d) {  // round-half-even of v / d, d > 0
     int64_t q = v >= 0 ? v / d : -((-v) / d);
     int64_t r = v - q * d;
@@ -336,6 +339,46 @@ std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups,
     return out;
 }
 
+// FP16-carrier constant planes.  Each balanced constant residue a splits as
+// a = c0 + 32 c1 (c1 = RNE(a / 32), |c0| <= 16, |c1| <= 32: FP16-exact).  Per
+// modulus: for the x_R half, digit pairs (a_R, a_I), for the x_I half
+// (-a_I, a_R), digits low to high; each plane is npad rows (outputs) x npad
+// FP16 values (K) in the no-swizzle K-major layout of 16-bit operands (8 x 8
+// core matrices of 16 bytes, LBO 128 between K neighbours, SBO 16 npad between
+// 8-row groups), so consecutive planes continue the rows of one operand.
+std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups, int K) {
+    const int npad = K <= 16 ? 16 : 32;
+    const size_t planeB = (size_t)npad * npad * 2, sbo = (size_t)16 * npad;
+    std::vector<uint8_t> out((size_t)groups * FP16_PLANES_PER_GROUP * planeB, 0);
+    size_t off = 0;
+    for (int g = 0; g < groups; g++)
+        for (int k = 0; k < NMOD; k++) {
+            const int64_t m = kModuli[k];
+            for (int h = 0; h < 2; h++)
+                for (int d = 0; d < 2; d++)
+                    for (int tb = 0; tb < 2; tb++) {
+                        const int sel = h == 0 ? (tb == 0 ? 0 : 1) : (tb == 0 ? 2 : 0);
+                        const size_t pbase = off + (size_t)((h * 2 + d) * 2 + tb) * planeB;
+                        for (int n = 0; n < K; n++)
+                            for (int j = 0; j < K; j++) {
+                                const int64_t *e = &F[(((size_t)g * K + n) * K + j) * 2];
+                                const int64_t a = sel == 0 ? e[0] : sel == 1 ? e[1] : -e[1];
+                                const int64_t r = modc(a, m);
+                                const int64_t v = 2 * r > m ? r - m : r;  // balanced
+                                const int64_t c1 = rne_div(v, 32);
+                                const int digit = (int)(d == 0 ? v - 32 * c1 : c1);
+                                const uint16_t hv = f16_of_small_int(digit);
+                                const size_t pos = pbase + (size_t)(n / 8) * sbo + (size_t)(j / 8) * 128 +
+                                                   (n % 8) * 16 + (j % 8) * 2;
+                                out[pos] = (uint8_t)(hv & 0xFF);
+                                out[pos + 1] = (uint8_t)(hv >> 8);
+                            }
+                    }
+            off += (size_t)8 * planeB;
+        }
+    return out;
+}
+
 // Phase A B-matrix: 48 rows (Re: 15 u-slices, 6 w-slices, 3 zero; Im: same)
 // x 32 K (Re residues 0..11, Im residues 12..23, 8 zero), FP16, K-major
 // canonical layout (LBO 128, SBO 512).
@@ -398,6 +441,13 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP8 constants: ") + cudaGetErrorString(e));
         std::vector<uint8_t> s1 = build_fp8_planes(t.Fq, 1, t.q);
         std::vector<uint8_t> s2 = build_fp8_planes(t.Fp, t.q, t.p);
+        e = upload(s1.data(), s1.size(), &t.fp8_s1);
+        if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
+    } else if (P->mode == OBFFT_MODE_FP16) {
+        e = fp8_upload_constants();
+        if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP16 constants: ") + cudaGetErrorString(e));
+        std::vector<uint8_t> s1 = build_fp16_planes(t.Fq, 1, t.q);
+        std::vector<uint8_t> s2 = build_fp16_planes(t.Fp, t.q, t.p);
         e = upload(s1.data(), s1.size(), &t.fp8_s1);
         if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
     } else if (P->mode == OBFFT_MODE_FP64_NATIVE) {
@@ -492,6 +542,7 @@ static float time_split(obfft_plan P, int n, int pp, int qq, double2 *buf, doubl
             double2 *dst = st == 1 ? tmp : outb;
             if (P->mode == OBFFT_MODE_INT8) launch_stage_int8(t, P->d_consts, g, st, src, dst, 0);
             else if (P->mode == OBFFT_MODE_FP8) launch_stage_fp8(t, P->d_consts, P->d_pab, P->d_status, g, st, src, dst, 0);
+            else if (P->mode == OBFFT_MODE_FP16) launch_stage_fp16(t, P->d_consts, P->d_pab, P->d_status, g, st, src, dst, 0);
             else launch_stage_fp64(t, g, st, src, dst, 0);
         }
         cudaEventRecord(b, 0);
@@ -509,7 +560,7 @@ static float time_split(obfft_plan P, int n, int pp, int qq, double2 *buf, doubl
 static void autotune_splits(obfft_plan P) {
     const char *env = getenv("OBFFT_AUTOTUNE");
     if (!env || env[0] != '1') return;
-    const int kmax = P->mode == OBFFT_MODE_FP8 ? 32 : KMAX;
+    const int kmax = (P->mode == OBFFT_MODE_FP8 || P->mode == OBFFT_MODE_FP16) ? 32 : KMAX;
     std::map<int, std::pair<int, int>> best;
     for (auto &gd : P->grids)
         for (int a = 0; a < 3; a++) {
@@ -597,7 +648,7 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
 }
 
 static obfft_status new_plan(int mode, obfft_plan *P) {
-    if (mode != OBFFT_MODE_FP8 && mode != OBFFT_MODE_INT8 && mode != OBFFT_MODE_FP64_NATIVE)
+    if (mode != OBFFT_MODE_FP8 && mode != OBFFT_MODE_INT8 && mode != OBFFT_MODE_FP64_NATIVE && mode != OBFFT_MODE_FP16)
         return set_error(OBFFT_ERR_ARG, "unknown mode");
     obfft_plan p = new obfft_plan_s();
     p->mode = mode;
@@ -630,7 +681,7 @@ extern "C" obfft_status obfft_plan_create(obfft_plan *out, int64_t n0, int64_t n
     if (n0 < 1 || n1 < 1 || n2 < 1 || batch < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
     GridDesc gd;
     gd.n[0] = n0; gd.n[1] = n1; gd.n[2] = n2;
-    const int kmax = mode == OBFFT_MODE_FP8 ? 32 : KMAX;
+    const int kmax = (mode == OBFFT_MODE_FP8 || mode == OBFFT_MODE_FP16) ? 32 : KMAX;
     for (int a = 0; a < 3; a++)
         if (!choose_split(gd.n[a], &gd.ax[a], kmax))
             return set_error(OBFFT_ERR_UNSUPPORTED_SIZE,
@@ -654,7 +705,7 @@ extern "C" obfft_status obfft_plan_create_many(obfft_plan *out, int count, const
         for (int a = 0; a < 3; a++) {
             gd.n[a] = dims[g * 3 + a];
             if (gd.n[a] < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
-            if (!choose_split(gd.n[a], &gd.ax[a], mode == OBFFT_MODE_FP8 ? 32 : KMAX))
+            if (!choose_split(gd.n[a], &gd.ax[a], (mode == OBFFT_MODE_FP8 || mode == OBFFT_MODE_FP16) ? 32 : KMAX))
                 return set_error(OBFFT_ERR_UNSUPPORTED_SIZE, "axis length " + std::to_string(gd.n[a]) +
                                                                  " does not factor within the mode's p, q limit");
         }
@@ -716,6 +767,8 @@ static obfft_status run_stage_geom(obfft_plan P, const AxisPlan &ap, const Stage
         e = launch_stage_int8(*t, P->d_consts, g, stage, in, out, s);
     else if (P->mode == OBFFT_MODE_FP8)
         e = launch_stage_fp8(*t, P->d_consts, P->d_pab, P->d_status, g, stage, in, out, s);
+    else if (P->mode == OBFFT_MODE_FP16)
+        e = launch_stage_fp16(*t, P->d_consts, P->d_pab, P->d_status, g, stage, in, out, s);
     else if (P->mode == OBFFT_MODE_FP64_NATIVE)
         e = launch_stage_fp64(*t, g, stage, in, out, s);
     else

@@ -50,7 +50,7 @@
 namespace obfft {
 
 // modulus kinds, in the order of kModuli
-enum : int { KIND_B11 = 0, KIND_SQ = 1, KIND_B9 = 2 };
+enum : int { KIND_B11 = 0, KIND_SQ = 1, KIND_B9 = 2, KIND_F16 = 3 };  // KIND_F16: the FP16 carrier
 __host__ __device__ constexpr int fp8_kind(int k) { return k < 3 ? KIND_B11 : (k < 9 ? KIND_SQ : KIND_B9); }
 __host__ __device__ constexpr int fp8_ndig(int k) { return fp8_kind(k) == KIND_B11 ? 3 : 2; }
 __host__ __device__ constexpr int fp8_ncls(int k) {
@@ -210,7 +210,24 @@ __device__ __forceinline__ void issue_modulus_nm(uint32_t dacc, uint32_t apl, ui
     }
 }
 
-constexpr int fp8_ncls_of_kind(int kind) { return kind == KIND_B11 ? 5 : (kind == KIND_SQ ? 2 : 3); }
+// FP16 carrier: per half (x_R, x_I) and K chunk of 16 elements one
+// tcgen05.mma kind::f16 (M = 128, N = 4 npad: digit c0 then c1, Re and Im rows
+// side by side, K = 16) into the two class accumulators (class 1 at 2 npad).
+template <int NPAD>
+__device__ __forceinline__ void issue_modulus_f16(uint32_t dacc, uint32_t apl, uint64_t bdesc) {
+    constexpr uint32_t planeB16 = NPAD * NPAD * 2 / 16;  // plane size in 16-byte descriptor units
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int kc = 0; kc < NPAD / 16; kc++)
+            tc_mma_f16_ta(dacc, apl + (uint32_t)(h * NPAD / 2 + kc * 8),
+                          bdesc + (uint64_t)(h * 4) * planeB16 + (uint64_t)(kc * 16), instr_desc(128, 4 * NPAD, 0),
+                          (h == 0 && kc == 0) ? 0u : 1u);
+}
+
+constexpr int fp8_ncls_of_kind(int kind) {
+    return kind == KIND_B11 ? 5 : ((kind == KIND_SQ || kind == KIND_F16) ? 2 : 3);
+}
 
 // Issue the TMEM loads of the class accumulators of this thread's OPT outputs
 // (completion: tmem_wait_ld, then regs_after_wait).
@@ -250,6 +267,19 @@ template <int KIND, int OPT>
 __device__ __forceinline__ void combine_classes(const uint32_t (&r)[5][OPT], const ModConsts &mc, int k,
                                                 float2 (&out)[OPT / 2]) {
     constexpr int NC = fp8_ncls_of_kind(KIND);
+    if constexpr (KIND == KIND_F16) {
+        // c0-class + 32 x c1-class exceeds 2^24: reduce the c1-class first
+        // (|x| < 2^22, so x - m RNE(x / m) is exact and within m/2 + 1)
+        const float2 nm2 = f2splat(-mc.fm[k]), im2 = f2splat(mc.finv[k]);
+#pragma unroll
+        for (int i = 0; i < OPT / 2; i++) {
+            const float2 c1 = make_float2(__uint_as_float(r[1][2 * i]), __uint_as_float(r[1][2 * i + 1]));
+            const float2 r1 = __ffma2_rn(nm2, rint2_mul(c1, im2), c1);
+            out[i] = __ffma2_rn(f2splat(32.0f), r1,
+                                make_float2(__uint_as_float(r[0][2 * i]), __uint_as_float(r[0][2 * i + 1])));
+        }
+        return;
+    }
     float wts[5];
     if constexpr (KIND == KIND_SQ) {
         wts[0] = 1.f;
@@ -382,12 +412,27 @@ __device__ __noinline__ double kulisch_finish_slow(uint32_t r0, uint32_t r1, uin
     return kulisch_finish_general(r0, r1, r2, r3, near != 0, et, c_fp8_mc);
 }
 
-template <int NPAD>
+// Constant-plane geometry of the two carriers.  E4M3 (CAR 0): planes of npad
+// rows x 32 bytes (K <= 32 one-byte digits), 4 x digits per modulus.  FP16
+// (CAR 1): planes of npad rows x npad FP16 values, 8 per modulus.
+template <int NPAD, int CAR>
+struct CarrierCfg {
+    static constexpr uint32_t PLANE_B = CAR ? NPAD * NPAD * 2 : NPAD * 32;
+    static constexpr uint32_t SBO = CAR ? 16 * NPAD : 256;  // bytes between 8-row groups
+    static constexpr int BUF_PLANES = CAR ? 8 : FP8_BPLANES;
+    static constexpr int PLANES_PER_GROUP = CAR ? FP16_PLANES_PER_GROUP : FP8_PLANES_PER_GROUP;
+    static constexpr uint32_t A_COLS = CAR ? NPAD : APL_COLS;  // TMEM columns of one A buffer
+    __host__ __device__ static constexpr int plane_offset(int k) { return CAR ? 8 * k : fp8_plane_offset(k); }
+    __host__ __device__ static constexpr int planes_of(int k) { return CAR ? 8 : 4 * fp8_ndig(k); }
+};
+
+template <int NPAD, int CAR>
 __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     stage_fp8_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab,
                      const ModConsts *__restrict__ gmc, ColMapT map, int64_t ncols, int K, int Kout,
                      const double2 *__restrict__ in, double2 *__restrict__ out, int *status, int pf_ahead) {
     using CF = Fp8Cfg<NPAD>;
+    using CC = CarrierCfg<NPAD, CAR>;
     constexpr int EPT = CF::EPT, OPT = CF::OPT, WPP = CF::WPP;
     constexpr int NSTEP = NMOD;  // one pipeline step per modulus
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -408,12 +453,16 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     const int group = map.group(cbase);
 
     const uint32_t stage_rows = (uint32_t)Kout * 128;
-    const uint32_t stage_bytes = (stage_rows >> 3) * PA_ROWB + 128;
+    // The E4M3 carrier keeps 128 zero bytes after the staging (read, times zero
+    // Phase-A rows, by the last row group's padded K chunk); the FP16 carrier
+    // has the Phase-A constants there instead (finite FP16 values), in the
+    // first constant buffer, loaded after the last modulus has used it.
+    const uint32_t stage_bytes = (stage_rows >> 3) * PA_ROWB + (CAR ? 0 : 128);
     uint8_t *sStage = smem;
     uint8_t *sB0 = smem + ((stage_bytes + 1023) & ~1023u);
-    const uint32_t planeB = NPAD * 32;
-    uint8_t *sPAB = sB0 + 2 * FP8_BPLANES * planeB;
-    const uint8_t *gplanes = planes + (size_t)group * FP8_PLANES_PER_GROUP * planeB;
+    constexpr uint32_t planeB = CC::PLANE_B;
+    uint8_t *sPAB = CAR ? sB0 : sB0 + 2 * CC::BUF_PLANES * planeB;
+    const uint8_t *gplanes = planes + (size_t)group * CC::PLANES_PER_GROUP * planeB;
 
     // The input tile is copied into the front of the Phase-A staging, which the
     // epilogues overwrite only after every thread has read its elements.
@@ -437,9 +486,11 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         __syncwarp();
         copy_input_tile(map, itile, K, in, sIn, smem_u32(&mbar[5]), lane);
         if (lane == 0) {
-            mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
-            tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
-            const uint32_t bytes0 = 4 * fp8_ndig(0) * planeB;
+            if (!CAR) {
+                mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
+                tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
+            }
+            const uint32_t bytes0 = CC::planes_of(0) * planeB;
             mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
             tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
         }
@@ -448,7 +499,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
         if (pf_ahead > 0 && nb < (int64_t)gridDim.x)
             prefetch_input_tile(map, input_tile(map, ncols, nb * 128), K, in, lane);
-    } else if (w == 3) {
+    } else if (w == 3 && !CAR) {
         reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[lane] = 0u;
     }
     tc_fence_before();
@@ -467,7 +518,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 tmem_st4_const(ta, 0u);
         }
     // K <= 16: bytes 16..31 of every A row stay zero (columns 4..7 of each of the 6 planes)
-    if (NPAD == 16 && qd == 0) {
+    if (NPAD == 16 && qd == 0 && !CAR) {
 #pragma unroll
         for (int b = 0; b < (int)N_ABUF; b++)
 #pragma unroll
@@ -528,6 +579,25 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             f = __fadd2_rn(f, off2);
             v[jj] = __ffma2_rn(nm2, rint2_mul(f, im2), f);  // balanced, [-m/2, m/2]
         }
+        if constexpr (CAR) {
+            // FP16 carrier: each balanced residue is one FP16 operand (|v| <= 1020);
+            // K-packed two per TMEM column, x_R at the buffer start, x_I npad / 2 later
+            uint32_t fR[EPT / 2], fI[EPT / 2];
+#pragma unroll
+            for (int i = 0; i < EPT / 2; i++) {
+                fR[i] = f16x2(v[2 * i].x, v[2 * i + 1].x);
+                fI[i] = f16x2(v[2 * i].y, v[2 * i + 1].y);
+            }
+            const uint32_t ta = tmem + lanebase + APL_BASE + (uint32_t)(k & 1) * CC::A_COLS + (uint32_t)(qd * EPT / 2);
+            if constexpr (EPT / 2 == 4) {
+                tmem_st4(ta, fR);
+                tmem_st4(ta + NPAD / 2, fI);
+            } else {
+                tmem_st2(ta, fR[0], fR[1]);
+                tmem_st2(ta + NPAD / 2, fI[0], fI[1]);
+            }
+            return;
+        }
         uint32_t wR[3][WPP], wI[3][WPP];
         const int kind = fp8_kind(k);
         if (kind == KIND_SQ)
@@ -554,22 +624,24 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // MMAs of modulus k, Re then Im part (thread 0 only).  Constant planes of
     // modulus k live in B buffer k & 1; B(k+1) is prefetched here, into the
     // buffer of modulus k-1, whose MMAs have completed.
-    const uint64_t bdesc0 = smem_desc(smem_u32(sB0), 128, 256);
-    const uint64_t bdesc1 = smem_desc(smem_u32(sB0 + FP8_BPLANES * planeB), 128, 256);
+    const uint64_t bdesc0 = smem_desc(smem_u32(sB0), 128, CC::SBO);
+    const uint64_t bdesc1 = smem_desc(smem_u32(sB0 + CC::BUF_PLANES * planeB), 128, CC::SBO);
     // Copy of the constant planes of modulus k into B buffer k & 1, whose
     // previous contents (modulus k - 2) are no longer read by any MMA.
     auto prefetch_b = [&](int k) {
-        const uint32_t bytes = 4 * fp8_ndig(k) * planeB;
+        const uint32_t bytes = CC::planes_of(k) * planeB;
         mbar_expect_tx(smem_u32(&mbar[k & 1]), bytes);
-        tma_bulk_g2s(smem_u32(sB0 + (k & 1) * FP8_BPLANES * planeB), gplanes + (size_t)fp8_plane_offset(k) * planeB,
+        tma_bulk_g2s(smem_u32(sB0 + (k & 1) * CC::BUF_PLANES * planeB), gplanes + (size_t)CC::plane_offset(k) * planeB,
                      bytes, smem_u32(&mbar[k & 1]));
     };
     auto issue = [&](int k) -> bool {
         if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
         const uint64_t bd = (k & 1) ? bdesc1 : bdesc0;
-        const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * APL_COLS;
+        const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * CC::A_COLS;
         const int kind = fp8_kind(k);
-        if (kind == KIND_SQ)
+        if constexpr (CAR)
+            issue_modulus_f16<NPAD>(tmem, apl, bd);
+        else if (kind == KIND_SQ)
             issue_modulus_nm<KIND_SQ>(tmem, apl, bd, NPAD);
         else if (kind == KIND_B9)
             issue_modulus_nm<KIND_B9>(tmem, apl, bd, NPAD);
@@ -600,7 +672,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         if (okm) {
             const uint32_t tre = tmem + lanebase + (uint32_t)(qd * OPT);
             const int kind = fp8_kind(k);
-            if (kind == KIND_SQ)
+            if constexpr (CAR)
+                epilogue_modulus<KIND_F16, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+            else if (kind == KIND_SQ)
                 epilogue_modulus<KIND_SQ, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
             else if (kind == KIND_B9)
                 epilogue_modulus<KIND_B9, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
@@ -624,6 +698,10 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             if (!issue(k + 1)) abort_flag = 1;
         } else if (tid == 32 && k + 2 < NSTEP) {
             prefetch_b(k + 2);
+        } else if (CAR && tid == 32 && k + 2 == NSTEP) {
+            // FP16 carrier: Phase-A constants into B buffer 0 (modulus k's, done)
+            mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
+            tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
         }
         // an abort raised by issue() is seen after the next step's barrier
     }
@@ -779,9 +857,14 @@ size_t fp8_smem_bytes(int Kout, int npad) {
     size_t stage_bytes = (size_t)Kout * 128 / 8 * PA_ROWB + 128;
     return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * FP8_BPLANES * (size_t)npad * 32 + PA_N * 64;
 }
+static size_t fp16_smem_bytes(int Kout, int npad) {
+    size_t stage_bytes = (size_t)Kout * 128 / 8 * PA_ROWB;  // Phase-A constants live in B buffer 0
+    return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * 8 * (size_t)npad * npad * 2;
+}
 
-cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
-                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s) {
+template <int CAR>
+static cudaError_t launch_stage_carrier(const AxisTables &t, const void *pab, int *status, const StageGeom &g,
+                                        int stage, const double2 *in, double2 *out, cudaStream_t s) {
     ColMapT map;
     map.stage = stage;
     map.L = g.L;
@@ -795,7 +878,7 @@ cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const vo
     const int npad = K <= 16 ? 16 : 32;
     const int64_t ncols = stage == 1 ? g.L * g.p : map.Lpad * g.q;
     const uint8_t *planes = (const uint8_t *)(stage == 1 ? t.fp8_s1 : t.fp8_s2);
-    size_t smem = fp8_smem_bytes(K, npad);
+    const size_t smem = CAR ? fp16_smem_bytes(K, npad) : fp8_smem_bytes(K, npad);
     int64_t blocks = (ncols + 127) / 128;
     if (blocks == 0) return cudaSuccess;
     int dev = 0, nsm = 0;
@@ -804,17 +887,29 @@ cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const vo
     err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     if (npad == 16) {
-        err = cudaFuncSetAttribute(stage_fp8_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(stage_fp8_kernel<16, CAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp8_kernel<16><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
-                                                                          ncols, K, K, in, out, status, nsm);
+        stage_fp8_kernel<16, CAR><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, nullptr, map, ncols, K, K, in, out, status, nsm);
     } else {
-        err = cudaFuncSetAttribute(stage_fp8_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp8_kernel<32><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(planes, (const uint8_t *)pab, dmc, map,
-                                                                          ncols, K, K, in, out, status, nsm);
+        stage_fp8_kernel<32, CAR><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, nullptr, map, ncols, K, K, in, out, status, nsm);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
+                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s) {
+    (void)dmc;
+    return launch_stage_carrier<0>(t, pab, status, g, stage, in, out, s);
+}
+
+cudaError_t launch_stage_fp16(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
+                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s) {
+    (void)dmc;
+    return launch_stage_carrier<1>(t, pab, status, g, stage, in, out, s);
 }
 
 }  // namespace obfft

@@ -17,7 +17,7 @@ def built():
     B.build()
 
 
-@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64", "fp16"])
 def test_gradient_matches_oracle_and_finite_differences(mode):
     from paper_2606_23698_gb300 import fft3_autograd, Plan
     batch, shape = 2, (16, 32, 16)

@@ -23,7 +23,7 @@ def built():
     B.build()
 
 
-@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64", "fp16"])
 def test_many_matches_single_plans_and_replays(mode):
     from paper_2606_23698_gb300 import Plan, PlanMany
     xs = [S.complex_gaussian(S.SEED_UNEVEN + i, d).to("cuda") for i, d in enumerate(DIMS)]

@@ -13,7 +13,7 @@ from tests.helpers import bits_equal, mismatch_report, oracle_full
 
 pytestmark = pytest.mark.gpu
 
-OZAKI_MODES = ["fp8", "int8"]
+OZAKI_MODES = ["fp8", "int8", "fp16"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -105,7 +105,7 @@ def test_wide_range_256_stage_sampled(mode):
     _check_pass_sampled(pl, x, shape, dir=-1, nsample=48)
 
 
-@pytest.mark.parametrize("mode", ["fp8"])
+@pytest.mark.parametrize("mode", ["fp8", "fp16"])
 def test_full_size_1024cube_sampled_and_parseval(mode):
     """The benchmark workload itself (1024^3, splits 32 x 32, uniform[-1,1)):
     every stage of every axis pass matches the oracle bit for bit on sampled
@@ -218,7 +218,7 @@ def test_device_timeout_reported_without_fault():
     assert bits_equal(y, oracle_full(x, splits_of(pl), -1))
 
 
-@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64"])
+@pytest.mark.parametrize("mode", ["fp8", "int8", "fp64", "fp16"])
 @pytest.mark.parametrize("shape,batch", [((96, 160, 144), 1), ((64, 48, 128), 2), ((8, 8, 8), 1)])
 def test_exec_host_matches_device_exec(mode, shape, batch):
     """obfft_exec_host (chunked copies overlapped with the first and last axis

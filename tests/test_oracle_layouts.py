@@ -20,6 +20,12 @@ def test_fp8_layout_exact_for_real_form_complex_product(m):
 
 
 @pytest.mark.parametrize("m", C.MODULI)
+def test_fp16_carrier_layout(m):
+    info = LY.check_fp16_carrier(m)
+    assert info["max_c0"] <= 16 and info["max_c1"] <= 32
+
+
+@pytest.mark.parametrize("m", C.MODULI)
 def test_int8_two_limb(m):
     LY.check_int8_two_limb(m)
 
