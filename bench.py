@@ -380,7 +380,7 @@ def main():
     # kernel on a 16 x 1024 x 1024 grid (256 MiB in and out, above L2):
     # dram__bytes_read.sum 268,664,320 + dram__bytes_write.sum 222,497,536,
     # scaled by the 64 times more columns of a 1024^3 launch
-    traffic = (268664320 + 222497536) * 64 if (mode == "fp8" and n == 1024) else None
+    traffic = (268791040 + 222775808) * 64 if (mode == "fp8" and n == 1024) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinst/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "kernel": f"stage_{mode}_kernel (axis 2, stage 1)", "kernel_ms": kern_ms,
