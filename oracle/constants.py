@@ -77,6 +77,31 @@ def capacity_bits(K: int, k: int = 53) -> float:
 
 
 # --------------------------------------------------------------------------
+# FP32-precision variant (Sec. "Ozaki-II for FP32" and the FP32 paragraph of
+# the hardware-ladder section): k = 24-bit significands, capacity budget 56
+# bits at K = 32, r = 6 moduli of the Rev-34 set with log2 M = 62.6, S = 8
+# byte slices, a 77-bit accumulator.
+# --------------------------------------------------------------------------
+# The paper names the size of the set but not its members.  Among the six-member
+# subsets of the Rev-34 set exactly one has log2 M = 62.6 (to +-0.05): this one.
+MODULI_FP32 = (2039, 2029, 2027, 1024, 961, 841)
+R_FP32 = len(MODULI_FP32)     # r = 6
+S_RAW_FP32 = 8                # S = ceil(63 / 8) byte slices of u_k
+# The paper fixes f only for the FP64 set.  Reading: f = 24 (three byte
+# slices), for which the lift error r max(v) 2^-f stays far below the 1/4 that
+# the two-sided correction needs (6 * 2047 * 2^-24 < 0.001).
+F_BITS_FP32 = 24
+S_FRAC_FP32 = 3
+SIGMA_F_EXP_FP32 = 23         # quantised constants carry 2^23 (24-bit signed significands)
+DATA_EXP_FP32 = 23            # data columns scaled so that |x~| < 2^24
+M_FP32 = modulus_product(MODULI_FP32)
+U_FP32 = idempotents(MODULI_FP32)
+W_FP32 = lift_weights(MODULI_FP32, F_BITS_FP32)
+U_SLICES_FP32 = [byte_slices(u, S_RAW_FP32) for u in U_FP32]
+W_SLICES_FP32 = [byte_slices(w, S_FRAC_FP32) for w in W_FP32]
+
+
+# --------------------------------------------------------------------------
 # High-precision cos / sin of 2*pi*m/N in integer fixed point.
 # --------------------------------------------------------------------------
 PREC = 240  # fractional bits of the fixed-point evaluation
@@ -152,26 +177,28 @@ def round_half_even_fixed(v: int, prec: int, scale_exp: int) -> int:
     return q
 
 
-def quantised_twiddle(m: int, N: int, sign: int = -1) -> tuple[int, int]:
-    """RNE(2^52 * omega) for omega = exp(sign * 2 pi i m / N): (Re, Im) integers."""
+def quantised_twiddle(m: int, N: int, sign: int = -1, scale_exp: int = SIGMA_F_EXP) -> tuple[int, int]:
+    """RNE(2^scale_exp * omega) for omega = exp(sign * 2 pi i m / N): (Re, Im) integers
+    (scale_exp = 52 for the FP64 method, 23 for its FP32 variant)."""
     c, s = cos_sin_2pi(m, N)
-    re = round_half_even_fixed(c, PREC, SIGMA_F_EXP)
-    im = round_half_even_fixed(s, PREC, SIGMA_F_EXP)
+    re = round_half_even_fixed(c, PREC, scale_exp)
+    im = round_half_even_fixed(s, PREC, scale_exp)
     return re, (im if sign > 0 else -im)
 
 
-def dft_matrix_q(q: int, sign: int = -1) -> list[list[tuple[int, int]]]:
-    """Quantised F_q[k2][j2] = RNE(2^52 omega_q^(j2 k2))."""
-    return [[quantised_twiddle(j2 * k2, q, sign) for j2 in range(q)] for k2 in range(q)]
+def dft_matrix_q(q: int, sign: int = -1, scale_exp: int = SIGMA_F_EXP) -> list[list[tuple[int, int]]]:
+    """Quantised F_q[k2][j2] = RNE(2^scale_exp omega_q^(j2 k2))."""
+    return [[quantised_twiddle(j2 * k2, q, sign, scale_exp) for j2 in range(q)] for k2 in range(q)]
 
 
-def fused_matrices_p(p: int, q: int, sign: int = -1) -> list[list[list[tuple[int, int]]]]:
-    """Quantised twiddle-fused F_p^(k2)[k1][j1] = RNE(2^52 omega_N^(j1 (q k1 + k2))), N = p q.
+def fused_matrices_p(p: int, q: int, sign: int = -1,
+                     scale_exp: int = SIGMA_F_EXP) -> list[list[list[tuple[int, int]]]]:
+    """Quantised twiddle-fused F_p^(k2)[k1][j1] = RNE(2^scale_exp omega_N^(j1 (q k1 + k2))), N = p q.
 
     omega_p^(j1 k1) omega_N^(j1 k2) = omega_N^(j1 (q k1 + k2)); the exponent is
     reduced mod N before evaluation (Eq. twiddle-fusion)."""
     N = p * q
-    return [[[quantised_twiddle((j1 * (q * k1 + k2)) % N, N, sign) for j1 in range(p)]
+    return [[[quantised_twiddle((j1 * (q * k1 + k2)) % N, N, sign, scale_exp) for j1 in range(p)]
              for k1 in range(p)] for k2 in range(q)]
 
 

@@ -20,6 +20,9 @@
  *                  (the definition the CRT must reach) and the two are
  *                  compared; the count of mismatches is returned.
  *   ob_ref_pack    RNE of a signed 128-bit integer times 2^e, gradual underflow.
+ *   ob_ref_stage32 / ob_ref_pack32   the same stage for the FP32-precision
+ *                  variant (Sec. "Ozaki-II for FP32"): complex64 columns,
+ *                  24-bit significands, r = 6 moduli, S = 8, f = 24.
  *   ob_ref_dft_dd_axis   direct O(N^2) DFT along the last axis in
  *                  double-double arithmetic (the high-precision reference).
  *   ob_ref_dft_dd_point  one output of the 3-D DFT in double-double.
@@ -344,6 +347,154 @@ int64_t ob_ref_stage(int64_t ncols, int K, int Kout,
                 yk[part] = ob_ref_pack((int64_t)(uint64_t)Rv, (int64_t)(uint64_t)((u128)Rv >> 64),
                                        e - 104);
             }
+        }
+    }
+    return mismatches;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32-precision variant (Sec. "Ozaki-II for FP32"): complex64 columns,     */
+/* 24-bit significands (constants RNE(2^23 omega), data x~ = x 2^(23-e)),    */
+/* r = 6 moduli, S = 8 byte slices of u_k, f = 24 (three slices of w_k).     */
+/* The lifted value fits the paper's 77-bit accumulator; here a 128-bit one. */
+/* ------------------------------------------------------------------------ */
+#define NMOD32 6
+#define S_RAW32 8
+#define S_FRAC32 3
+
+typedef struct {
+    int64_t m[NMOD32];
+    uint8_t us[NMOD32][S_RAW32];
+    uint8_t ws[NMOD32][S_FRAC32];
+    uint64_t M;
+} ob_consts32;
+
+typedef struct {
+    uint16_t *v;       /* [ncols][Kout][2][NMOD32]   canonical residues  */
+    int64_t *P;        /* [ncols][Kout][2][S_RAW32]  Phase A slice sums  */
+    int64_t *Q;        /* [ncols][Kout][2][S_FRAC32] lift partials        */
+    int64_t *zhat;     /* [ncols][Kout][2]                                */
+    int64_t *R;        /* [ncols][Kout][2]           lifted R (|R| < 2^63) */
+} ob_dump32;
+
+/* RNE(R * 2^e) to binary32, gradual underflow (quantum 2^-149), overflow to
+ * infinity.  Done in integers: the one rounding of the FP32 pipeline. */
+float ob_ref_pack32(int64_t Rv, int e) {
+    if (Rv == 0) return 0.0f;
+    int neg = Rv < 0;
+    u128 a = neg ? (u128)(-(i128)Rv) : (u128)Rv;
+    int L = bitlen_u128(a);
+    int d = L - 24;            /* keep 24 significant bits */
+    int d_sub = -149 - e;      /* and no bit below 2^-149 */
+    if (d_sub > d) d = d_sub;
+    u128 q;
+    if (d <= 0) {
+        q = a;
+        d = 0;
+    } else if (d > L) {
+        q = 0;
+    } else {
+        q = a >> d;
+        u128 rem = a & ((((u128)1) << d) - 1);
+        u128 half = ((u128)1) << (d - 1);
+        if (rem > half || (rem == half && (q & 1))) q += 1;
+    }
+    /* q <= 2^24: q 2^(e+d) is a binary32 value or beyond its range; form it in
+       double (exact) and narrow (exact, or infinity when too large). */
+    double r = ldexp((double)(uint64_t)q, e + d);
+    float f = (float)r;
+    return neg ? -f : f;
+}
+
+/* y[c][k] = RNE32( 2^(e_c - 46) * sum_j F~[g(c)][k][j] * x~[c][j] ) */
+int64_t ob_ref_stage32(int64_t ncols, int K, int Kout,
+                       const float *x,         /* [ncols][K][2] */
+                       const int64_t *Ftab,    /* [ngroups][Kout][K][2], |entry| <= 2^23 */
+                       const int32_t *group,   /* [ncols] or NULL */
+                       const ob_consts32 *c,
+                       int use_crt,
+                       float *y,               /* [ncols][Kout][2] */
+                       ob_dump32 *dump) {
+    int64_t mismatches = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : mismatches)
+    for (int64_t col = 0; col < ncols; col++) {
+        const float *xc = x + col * (int64_t)K * 2;
+        int g = group ? group[col] : 0;
+        const int64_t *F = Ftab + (int64_t)g * Kout * K * 2;
+        /* deconstruction: one power of two per column, common to Re and Im */
+        double amax = 0.0;
+        for (int j = 0; j < 2 * K; j++) {
+            double a = fabs((double)xc[j]);
+            if (a > amax) amax = a;
+        }
+        int e = amax > 0.0 ? ilogb(amax) : 0;
+        int64_t xt[2 * 64];
+        for (int j = 0; j < 2 * K; j++) xt[j] = (int64_t)rint(ldexp((double)xc[j], 23 - e));
+
+        for (int k = 0; k < Kout; k++) {
+            const int64_t *Fk = F + (int64_t)k * K * 2;
+            i128 Cre = 0, Cim = 0;
+            for (int j = 0; j < K; j++) {
+                i128 fr = Fk[2 * j], fi = Fk[2 * j + 1];
+                i128 xr = xt[2 * j], xi = xt[2 * j + 1];
+                Cre += fr * xr - fi * xi;
+                Cim += fr * xi + fi * xr;
+            }
+            i128 Rout[2] = {Cre, Cim};
+            if (use_crt) {
+                int64_t v[2][NMOD32];
+                for (int i = 0; i < NMOD32; i++) {
+                    int64_t m = c->m[i];
+                    int64_t D = 0, Ev = 0, Fv = 0;
+                    for (int j = 0; j < K; j++) {
+                        int64_t ar = modc(Fk[2 * j], m), ai = modc(Fk[2 * j + 1], m);
+                        int64_t as = modc((i128)Fk[2 * j] + Fk[2 * j + 1], m);
+                        int64_t br = modc(xt[2 * j], m), bi = modc(xt[2 * j + 1], m);
+                        int64_t bs = modc((i128)xt[2 * j] + xt[2 * j + 1], m);
+                        D += ar * br;
+                        Ev += ai * bi;
+                        Fv += as * bs;
+                    }
+                    v[0][i] = modc((i128)(D % m) - (Ev % m), m);
+                    v[1][i] = modc((i128)(Fv % m) - (D % m) - (Ev % m), m);
+                }
+                for (int part = 0; part < 2; part++) {
+                    int64_t P[S_RAW32], Q[S_FRAC32];
+                    for (int s = 0; s < S_RAW32; s++) {
+                        P[s] = 0;
+                        for (int i = 0; i < NMOD32; i++) P[s] += v[part][i] * c->us[i][s];
+                    }
+                    for (int t = 0; t < S_FRAC32; t++) {
+                        Q[t] = 0;
+                        for (int i = 0; i < NMOD32; i++) Q[t] += v[part][i] * c->ws[i][t];
+                    }
+                    /* Phase B: E = sum_s P_s 256^s, zhat = round(2^-24 sum_t Q_t 256^t),
+                       R = E - zhat M, two-sided centered correction */
+                    i128 E = 0, zacc = 0;
+                    for (int s = 0; s < S_RAW32; s++) E += (i128)P[s] << (8 * s);
+                    for (int t = 0; t < S_FRAC32; t++) zacc += (i128)Q[t] << (8 * t);
+                    i128 zsum = zacc + ((i128)1 << 23);
+                    i128 zq = zsum / ((i128)1 << 24);
+                    if (zq * ((i128)1 << 24) > zsum) zq -= 1;
+                    i128 Mv = (i128)c->M;
+                    i128 Rv = E - zq * Mv;
+                    if (2 * Rv >= Mv) Rv -= Mv;
+                    if (2 * Rv < -Mv) Rv += Mv;
+                    int64_t base = (col * Kout + k) * 2 + part;
+                    if (dump) {
+                        if (dump->v)
+                            for (int i = 0; i < NMOD32; i++) dump->v[base * NMOD32 + i] = (uint16_t)v[part][i];
+                        if (dump->P) memcpy(dump->P + base * S_RAW32, P, sizeof P);
+                        if (dump->Q) memcpy(dump->Q + base * S_FRAC32, Q, sizeof Q);
+                        if (dump->zhat) dump->zhat[base] = (int64_t)zq;
+                        if (dump->R) dump->R[base] = (int64_t)Rv;
+                    }
+                    if (Rv != Rout[part]) mismatches++;
+                    Rout[part] = Rv;
+                }
+            }
+            float *yk = y + (col * Kout + k) * 2;
+            for (int part = 0; part < 2; part++) yk[part] = ob_ref_pack32((int64_t)Rout[part], e - 46);
         }
     }
     return mismatches;

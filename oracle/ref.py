@@ -44,6 +44,17 @@ class _Consts(ctypes.Structure):
                 ("M", ctypes.c_uint32 * 4)]
 
 
+class _Consts32(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64 * 6),
+                ("us", (ctypes.c_uint8 * 8) * 6),
+                ("ws", (ctypes.c_uint8 * 3) * 6),
+                ("M", ctypes.c_uint64)]
+
+
+class _Dump32(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("v", "P", "Q", "zhat", "R")]
+
+
 class _Dump(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in
                 ("col_exp", "xt", "def_", "v", "P", "Q", "zhat", "Rlimbs")]
@@ -60,6 +71,12 @@ def lib():
     L.ob_ref_stage.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Consts),
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_Dump)]
+    L.ob_ref_stage32.restype = ctypes.c_int64
+    L.ob_ref_stage32.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Consts32),
+                                 ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(_Dump32)]
+    L.ob_ref_pack32.restype = ctypes.c_float
+    L.ob_ref_pack32.argtypes = [ctypes.c_int64, ctypes.c_int]
     L.ob_ref_pack.restype = ctypes.c_double
     L.ob_ref_pack.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
     L.ob_ref_kulisch.restype = None
@@ -90,19 +107,35 @@ def consts(moduli=C.MODULI) -> _Consts:
     return c
 
 
+def consts32() -> _Consts32:
+    c = _Consts32()
+    for k, m in enumerate(C.MODULI_FP32):
+        c.m[k] = m
+        for s_ in range(C.S_RAW_FP32):
+            c.us[k][s_] = C.U_SLICES_FP32[k][s_]
+        for t in range(C.S_FRAC_FP32):
+            c.ws[k][t] = C.W_SLICES_FP32[k][t]
+    c.M = C.M_FP32
+    return c
+
+
+# Per-precision parameters: numpy complex type and the constants' scale exponent.
+PRECISIONS = {"fp64": (np.complex128, C.SIGMA_F_EXP), "fp32": (np.complex64, C.SIGMA_F_EXP_FP32)}
+
+
 # --------------------------------------------------------------------------
 # Tables
 # --------------------------------------------------------------------------
 @lru_cache(maxsize=None)
-def table_q(q: int, sign: int) -> np.ndarray:
+def table_q(q: int, sign: int, scale_exp: int = C.SIGMA_F_EXP) -> np.ndarray:
     """F_q as int64 [1][q][q][2] (k2, j2, re/im)."""
-    return np.ascontiguousarray(np.array(C.dft_matrix_q(q, sign), dtype=np.int64)[None])
+    return np.ascontiguousarray(np.array(C.dft_matrix_q(q, sign, scale_exp), dtype=np.int64)[None])
 
 
 @lru_cache(maxsize=None)
-def table_p(p: int, q: int, sign: int) -> np.ndarray:
+def table_p(p: int, q: int, sign: int, scale_exp: int = C.SIGMA_F_EXP) -> np.ndarray:
     """F_p^(k2) as int64 [q][p][p][2] (k2, k1, j1, re/im)."""
-    return np.ascontiguousarray(np.array(C.fused_matrices_p(p, q, sign), dtype=np.int64))
+    return np.ascontiguousarray(np.array(C.fused_matrices_p(p, q, sign, scale_exp), dtype=np.int64))
 
 
 @lru_cache(maxsize=None)
@@ -148,32 +181,68 @@ def stage(cols: np.ndarray, Ftab: np.ndarray, group: np.ndarray | None = None,
     return y, mism, arrays
 
 
-def bailey_lines(x: np.ndarray, p: int, q: int, sign: int = -1, use_crt: bool = True):
-    """Ozaki-Bailey 1-D transform of every row of x (complex128 [L][N], N = p q).
+def stage32(cols: np.ndarray, Ftab: np.ndarray, group: np.ndarray | None = None,
+            use_crt: bool = True, dump: bool = False):
+    """The FP32-precision variant of `stage`: complex64 columns, constants
+    RNE(2^23 omega), six moduli.  Returns (y complex64 [ncols][Kout], mismatches, dump)."""
+    cols = np.ascontiguousarray(cols, dtype=np.complex64)
+    ncols, K = cols.shape
+    Kout = Ftab.shape[1]
+    assert Ftab.shape[2] == K and K <= 64
+    y = np.empty((ncols, Kout), dtype=np.complex64)
+    g = None if group is None else np.ascontiguousarray(group, dtype=np.int32)
+    d = _Dump32()
+    arrays = None
+    if dump:
+        arrays = dict(v=np.zeros((ncols, Kout, 2, 6), np.uint16),
+                      P=np.zeros((ncols, Kout, 2, 8), np.int64),
+                      Q=np.zeros((ncols, Kout, 2, 3), np.int64),
+                      zhat=np.zeros((ncols, Kout, 2), np.int64),
+                      R=np.zeros((ncols, Kout, 2), np.int64))
+        for k, a in arrays.items():
+            setattr(d, k, a.ctypes.data)
+    cst = consts32()
+    mism = lib().ob_ref_stage32(ncols, K, Kout, _ptr(cols.view(np.float32)),
+                                _ptr(np.ascontiguousarray(Ftab)), _ptr(g), ctypes.byref(cst),
+                                1 if use_crt else 0, _ptr(y.view(np.float32)), ctypes.byref(d))
+    return y, mism, arrays
+
+
+def _stage_of(prec: str):
+    return stage if prec == "fp64" else stage32
+
+
+def bailey_lines(x: np.ndarray, p: int, q: int, sign: int = -1, use_crt: bool = True,
+                 prec: str = "fp64"):
+    """Ozaki-Bailey 1-D transform of every row of x ([L][N], N = p q; complex128
+    for prec "fp64", complex64 for the FP32 variant "fp32").
 
     Returns (Y [L][N], mismatches)."""
+    ctype, sexp = PRECISIONS[prec]
+    x = np.asarray(x, dtype=ctype)
     L, N = x.shape
     assert N == p * q
     if N == 1:
         return x.copy(), 0
+    st = _stage_of(prec)
     # stage 1: columns (l, j1) over j2; x[l, j1 + p j2] -> view [L][q][p]
     c1 = x.reshape(L, q, p).transpose(0, 2, 1).reshape(L * p, q)
-    y1, m1, _ = stage(c1, table_q(q, sign), None, use_crt)
+    y1, m1, _ = st(c1, table_q(q, sign, sexp), None, use_crt)
     y1 = y1.reshape(L, p, q)                        # Y'[l][j1][k2]
     # stage 2: columns (l, k2) over j1, matrix F_p^(k2)
     c2 = y1.transpose(0, 2, 1).reshape(L * q, p)
     grp = np.tile(np.arange(q, dtype=np.int32), L)
-    z, m2, _ = stage(c2, table_p(p, q, sign), grp, use_crt)
+    z, m2, _ = st(c2, table_p(p, q, sign, sexp), grp, use_crt)
     z = z.reshape(L, q, p)                          # Z[l][k2][k1]
     Y = z.transpose(0, 2, 1).reshape(L, N)          # Y[k2 + q k1]
     return np.ascontiguousarray(Y), m1 + m2
 
 
-def obfft3d(x: np.ndarray, splits, sign: int = -1, use_crt: bool = True):
+def obfft3d(x: np.ndarray, splits, sign: int = -1, use_crt: bool = True, prec: str = "fp64"):
     """3-D Ozaki-Bailey transform of x [..., n0, n1, n2]; splits = ((p0,q0),(p1,q1),(p2,q2)).
 
     Axis 2 first, then 1, then 0.  Returns (Y, total mismatches)."""
-    x = np.asarray(x, dtype=np.complex128)
+    x = np.asarray(x, dtype=PRECISIONS[prec][0])
     y = x
     mism = 0
     for axis in (2, 1, 0):
@@ -182,7 +251,7 @@ def obfft3d(x: np.ndarray, splits, sign: int = -1, use_crt: bool = True):
         p, q = splits[axis]
         moved = np.moveaxis(y, ax, -1)
         shp = moved.shape
-        Y, m = bailey_lines(np.ascontiguousarray(moved).reshape(-1, n), p, q, sign, use_crt)
+        Y, m = bailey_lines(np.ascontiguousarray(moved).reshape(-1, n), p, q, sign, use_crt, prec)
         mism += m
         y = np.moveaxis(Y.reshape(shp), -1, ax)
     return np.ascontiguousarray(y), mism
@@ -196,6 +265,11 @@ def pack(R: int, e: int) -> float:
     if hi >= 1 << 63:
         hi -= 1 << 64
     return lib().ob_ref_pack(lo, hi, e)
+
+
+def pack32(R: int, e: int) -> np.float32:
+    """RNE(R 2^e) to binary32 (|R| < 2^63), the FP32 variant's single rounding."""
+    return np.float32(lib().ob_ref_pack32(int(R), int(e)))
 
 
 def kulisch(P: np.ndarray, Q: np.ndarray, moduli=C.MODULI):
