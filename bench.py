@@ -158,6 +158,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# -------------------------------------------------- FP32-precision variant --
+def fp32_variant(torch, Plan, x, y64, stream):
+    """1024^3 complex64 forward transform in the FP32 Ozaki variant (r = 6) and
+    the native FP32 comparator: ms per transform (CUDA events, 2 steps after a
+    warm-up), one stage launch of the Ozaki kernel, and the relative difference
+    of each result to the native FP64 transform of the same (widened) input."""
+    x32 = x.to(torch.complex64)
+    y32 = torch.empty_like(x32)
+    ref = y64.to(torch.complex64)  # FP64 result rounded: the binary32 target
+    out = {}
+    for m in ("fp32", "fp32native"):
+        pl = Plan(*x.shape, mode=m)
+        pl.exec(x32, y32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            pl.exec(x32, y32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res = {"ms": e0.elapsed_time(e1) / 2,
+               "rel_diff_vs_fp64_native": float(torch.linalg.vector_norm((y32 - ref).to(torch.complex128)) /
+                                                torch.linalg.vector_norm(ref.to(torch.complex128)))}
+        if m == "fp32":
+            scratch = torch.empty_like(x32)
+            pl.exec_stage(2, 1, x32, scratch)
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            for _ in range(3):
+                pl.exec_stage(2, 1, x32, scratch)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            res["stage_kernel_ms"] = k0.elapsed_time(k1) / 3
+            del scratch
+        out[m] = res
+        pl.close()
+    del x32, y32, ref
+    torch.cuda.empty_cache()
+    out["workload"] = "1024^3 complex64 forward 3-D FFT, splits 32x32, the complex128 input rounded"
+    return out
+
+
 # ------------------------------------------------------- side configurations --
 def side_configs(torch, Plan, PlanMany, S, mode):
     """The other workloads of the benchmark set, measured at their own sizes:
@@ -316,6 +358,8 @@ def main():
     # comparator modes at the same size
     modes = {mode: ms_step}
     others = [m for m in ("fp8", "int8", "fp16", "fp64") if m != mode]
+    diff = 0.0
+    y64 = None
     for m in others:
         pl2, ms2 = time_mode(m, max(1, min(args.steps, 2)), 1)
         modes[m] = ms2 / max(1, min(args.steps, 2))
@@ -324,8 +368,15 @@ def main():
             pl2.exec(x, y64)
             torch.cuda.synchronize()
             diff = float(torch.linalg.vector_norm(y_main - y64) / torch.linalg.vector_norm(y64))
-            del y64
         pl2.close()
+    if y64 is None:
+        y64 = y_main
+
+    # the FP32-precision variant at the same size (after the e2e timing below):
+    # complex64 copy of the input, Ozaki FP32 and native FP32, errors against
+    # the native FP64 transform
+    y64_keep = y64 if (rank == 0 and not args.no_extra) else None
+    del y64
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -350,6 +401,11 @@ def main():
         e2e = {"value": ems, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "call": "obfft_exec_host"}
         del hx, hy
+
+    fp32 = None
+    if y64_keep is not None:
+        fp32 = fp32_variant(torch, Plan, x, y64_keep, stream)
+    del y64_keep
 
     extra = None
     if not args.no_extra and rank == 0 and n == 1024:
@@ -378,7 +434,7 @@ def main():
     fp8_ops = 2 * N3 * (228 * 32 + 32 * 48)
     # DRAM bytes per FP8 stage launch at 1024^3 from one ncu capture of the same
     # kernel on a 16 x 1024 x 1024 grid (256 MiB in and out, above L2):
-    # dram__bytes_read.sum 268,664,320 + dram__bytes_write.sum 222,497,536,
+    # dram__bytes_read.sum 268,791,040 + dram__bytes_write.sum 222,775,808,
     # scaled by the 64 times more columns of a 1024^3 launch
     traffic = (268791040 + 222775808) * 64 if (mode == "fp8" and n == 1024) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinst/s",
@@ -399,14 +455,14 @@ def main():
     line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp8": "e4m3", "int8": "s8", "fp64": "f64"}[mode],
+            "dtype": {"fp8": "e4m3", "int8": "s8", "fp16": "f16", "fp64": "f64"}[mode],
             "data": "synthetic",
             "config": {"workload": f"{n}^3 complex128 forward 3-D FFT, splits 32x32 per axis",
                        "mode": mode, "seed": 20260003, "l2": "inputs larger than L2",
                        "parallelism": "replicas" if world > 1 else "single"},
             "gflops_5nlogn": gflops, "modes_ms": modes, "rel_diff_vs_fp64_native": diff,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches, "side_configs": extra}
+            "gpu_launches": launches, "side_configs": extra, "fp32_variant": fp32}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -14,7 +14,9 @@
  *      inverse  (dir = +1): the conjugate kernel, unnormalised (so the inverse
  *               is also the adjoint of the forward transform).
  *  - Layout: contiguous C-order [batch][n0][n1][n2] complex128, interleaved
- *    (re, im) doubles, 16-byte aligned.  Axis 2 is transformed first, then 1,
+ *    (re, im) doubles, 16-byte aligned; complex64 (interleaved floats, still
+ *    16-byte aligned) for the FP32-precision modes OBFFT_MODE_FP32 and
+ *    OBFFT_MODE_FP32_NATIVE.  Axis 2 is transformed first, then 1,
  *    then 0; each axis of length n = p * q uses the Bailey indices
  *    j = j1 + p j2, k = k2 + q k1 with 1 <= p, q <= 64.
  *  - Pointers passed to obfft_exec / obfft_exec_many are DEVICE pointers
@@ -58,7 +60,15 @@ typedef enum {
     /* residue GEMMs on tcgen05 FP16 tensor cores (kind::f16), the FP16-carrier
        variant: each balanced data residue is one FP16 operand (no digit split),
        each constant residue two FP16 digits c0 + 32 c1; Phase A as in FP8 mode */
-    OBFFT_MODE_FP16 = 3
+    OBFFT_MODE_FP16 = 3,
+    /* FP32-precision variant (Sec. "Ozaki-II for FP32"): complex64 in and out,
+       24-bit significands, r = 6 moduli {2039, 2029, 2027, 1024, 961, 841},
+       S = 8 byte slices, f = 24; residue GEMMs on tcgen05 FP16 tensor cores
+       (FP16 carrier), Phase A on tcgen05 FP16, one correctly rounded binary32
+       conversion per stage output.  Axis factors p, q <= 32. */
+    OBFFT_MODE_FP32 = 4,
+    /* comparator of the FP32 variant: plain FP32 six-step FFT on complex64 */
+    OBFFT_MODE_FP32_NATIVE = 5
 } obfft_mode;
 
 /*
@@ -178,6 +188,15 @@ obfft_status obfft_host_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int6
  */
 obfft_status obfft_host_crt_constants(uint32_t *moduli, uint8_t *u_slices, uint8_t *w_slices,
                                       uint32_t *M4);
+
+/*
+ * The same two introspection calls for the FP32-precision variant:
+ * RNE(2^23 exp(dir 2 pi i m / N)) (24-bit signed significands), and
+ * moduli[6], u_slices[6][8], w_slices[6][3] (w_k = round(2^24 u_k / M)) and M
+ * (< 2^63).  Caller-owned host buffers; OBFFT_ERR_ARG for bad arguments.
+ */
+obfft_status obfft_host_twiddle32(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im);
+obfft_status obfft_host_crt_constants32(uint32_t *moduli, uint8_t *u_slices, uint8_t *w_slices, uint64_t *M);
 
 /*
  * Largest grid (n0 * n1 * n2 complex128 values) obfft_exec_fp64_noalloc accepts.

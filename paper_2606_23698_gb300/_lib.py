@@ -25,15 +25,19 @@ OBFFT_MODE_FP8 = 0
 OBFFT_MODE_INT8 = 1
 OBFFT_MODE_FP64_NATIVE = 2
 OBFFT_MODE_FP16 = 3
+OBFFT_MODE_FP32 = 4
+OBFFT_MODE_FP32_NATIVE = 5
 MODES = {"fp8": OBFFT_MODE_FP8, "int8": OBFFT_MODE_INT8, "fp64": OBFFT_MODE_FP64_NATIVE,
-         "fp16": OBFFT_MODE_FP16}
+         "fp16": OBFFT_MODE_FP16, "fp32": OBFFT_MODE_FP32, "fp32native": OBFFT_MODE_FP32_NATIVE}
+# modes whose data are complex64 (the FP32-precision variant and its comparator)
+COMPLEX64_MODES = (OBFFT_MODE_FP32, OBFFT_MODE_FP32_NATIVE)
 
 # every symbol include/obfft.h declares
 EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_splits",
            "obfft_plan_create_many", "obfft_exec_many", "obfft_exec_stage", "obfft_last_error",
            "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants",
            "obfft_exec_fp64_noalloc", "obfft_plan_status", "obfft_selftest_bounded_wait",
-           "obfft_exec_host")
+           "obfft_exec_host", "obfft_host_twiddle32", "obfft_host_crt_constants32")
 
 _lib = None
 
@@ -72,6 +76,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_host_twiddle.restype = i32
     L.obfft_host_crt_constants.argtypes = [vp, vp, vp, vp]
     L.obfft_host_crt_constants.restype = i32
+    L.obfft_host_twiddle32.argtypes = [i64, i64, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.obfft_host_twiddle32.restype = i32
+    L.obfft_host_crt_constants32.argtypes = [vp, vp, vp, vp]
+    L.obfft_host_crt_constants32.restype = i32
     L.obfft_plan_status.argtypes = [vp, vp]
     L.obfft_plan_status.restype = i32
     L.obfft_selftest_bounded_wait.argtypes = [vp, vp]
@@ -145,6 +153,24 @@ def obfft_plan_status(plan: int, stream: int = 0) -> None:
 
 def obfft_selftest_bounded_wait(plan: int, stream: int = 0) -> None:
     check(load().obfft_selftest_bounded_wait(plan, stream))
+
+
+def obfft_host_twiddle32(m: int, N: int, dir: int):
+    """RNE(2^23 exp(dir 2 pi i m / N)) of the FP32-precision plans (host only)."""
+    re, im = ctypes.c_int64(), ctypes.c_int64()
+    check(load().obfft_host_twiddle32(m, N, dir, ctypes.byref(re), ctypes.byref(im)))
+    return re.value, im.value
+
+
+def obfft_host_crt_constants32():
+    """(moduli[6], u_slices[6][8], w_slices[6][3], M) of the FP32-precision variant (host only)."""
+    mod = (ctypes.c_uint32 * 6)()
+    us = (ctypes.c_uint8 * 48)()
+    ws = (ctypes.c_uint8 * 18)()
+    M = ctypes.c_uint64()
+    check(load().obfft_host_crt_constants32(mod, us, ws, ctypes.byref(M)))
+    return list(mod), [list(us[8 * k:8 * k + 8]) for k in range(6)], \
+        [list(ws[3 * k:3 * k + 3]) for k in range(6)], M.value
 
 
 def obfft_last_error() -> str:

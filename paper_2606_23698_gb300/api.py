@@ -1,9 +1,10 @@
 """torch-tensor layer over the C ABI: plans as objects, tensors as pointers.
 
 Only argument marshalling: the transform itself runs in libobfft.so, on the
-GPU.  exec / exec_stage take contiguous complex128 CUDA tensors; exec_host takes
-host tensors, which the library copies to and from the GPU around (and
-overlapped with) the same GPU transform.  No CPU compute path exists.
+GPU.  exec / exec_stage take contiguous CUDA tensors (complex128, or complex64
+for the FP32-precision modes "fp32" and "fp32native"); exec_host takes host
+tensors, which the library copies to and from the GPU around (and overlapped
+with) the same GPU transform.  No CPU compute path exists.
 """
 from __future__ import annotations
 
@@ -18,11 +19,16 @@ def _mode(mode) -> int:
     return int(mode)
 
 
-def _check_tensor(t: torch.Tensor, numel: int, name: str) -> None:
+def dtype_of(mode) -> torch.dtype:
+    """Element type of a mode's data: complex64 for the FP32-precision modes."""
+    return torch.complex64 if _mode(mode) in _lib.COMPLEX64_MODES else torch.complex128
+
+
+def _check_tensor(t: torch.Tensor, numel: int, name: str, dtype=torch.complex128) -> None:
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor (no CPU path)")
-    if t.dtype != torch.complex128:
-        raise TypeError(f"{name} must be complex128")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if t.numel() != numel:
@@ -30,11 +36,13 @@ def _check_tensor(t: torch.Tensor, numel: int, name: str) -> None:
 
 
 class Plan:
-    """batch x n0 x n1 x n2 complex128 transform plan on the current CUDA device."""
+    """batch x n0 x n1 x n2 transform plan on the current CUDA device (complex128
+    data, complex64 for the FP32-precision modes)."""
 
     def __init__(self, n0: int, n1: int, n2: int, batch: int = 1, mode="fp8"):
         self.shape = (batch, n0, n1, n2)
         self.mode = _mode(mode)
+        self.dtype = dtype_of(self.mode)
         self.device = torch.cuda.current_device()
         self.handle = _lib.obfft_plan_create(n0, n1, n2, batch, self.mode)
 
@@ -48,10 +56,10 @@ class Plan:
 
     def exec(self, x: torch.Tensor, out: torch.Tensor | None = None, dir: int = -1,
              stream: torch.cuda.Stream | None = None) -> torch.Tensor:
-        _check_tensor(x, self.numel, "input")
+        _check_tensor(x, self.numel, "input", self.dtype)
         if out is None:
             out = torch.empty_like(x)
-        _check_tensor(out, self.numel, "output")
+        _check_tensor(out, self.numel, "output", self.dtype)
         s = stream if stream is not None else torch.cuda.current_stream(x.device)
         _lib.obfft_exec(self.handle, x.data_ptr(), out.data_ptr(), dir, s.cuda_stream)
         return out
@@ -59,23 +67,24 @@ class Plan:
     def exec_host(self, x: torch.Tensor, out: torch.Tensor | None = None, dir: int = -1,
                   stream: torch.cuda.Stream | None = None) -> torch.Tensor:
         """Host-to-host transform (obfft_exec_host): x and out are contiguous
-        complex128 CPU tensors, ideally pinned; the copies overlap the transform.
-        The output is complete once `stream` (default: current) is synchronised."""
-        if x.device.type != "cpu" or x.dtype != torch.complex128 or not x.is_contiguous() \
+        CPU tensors of the plan's dtype, ideally pinned; the copies overlap the
+        transform.  The output is complete once `stream` (default: current) is
+        synchronised."""
+        if x.device.type != "cpu" or x.dtype != self.dtype or not x.is_contiguous() \
                 or x.numel() != self.numel:
-            raise ValueError(f"input must be a contiguous complex128 CPU tensor of {self.numel} elements")
+            raise ValueError(f"input must be a contiguous {self.dtype} CPU tensor of {self.numel} elements")
         if out is None:
             out = torch.empty(x.shape, dtype=x.dtype, pin_memory=x.is_pinned())
-        if out.device.type != "cpu" or out.dtype != torch.complex128 or not out.is_contiguous() \
+        if out.device.type != "cpu" or out.dtype != self.dtype or not out.is_contiguous() \
                 or out.numel() != self.numel:
-            raise ValueError(f"output must be a contiguous complex128 CPU tensor of {self.numel} elements")
+            raise ValueError(f"output must be a contiguous {self.dtype} CPU tensor of {self.numel} elements")
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         _lib.obfft_exec_host(self.handle, x.data_ptr(), out.data_ptr(), dir, s.cuda_stream)
         return out
 
     def exec_stage(self, axis: int, stage: int, x: torch.Tensor, out: torch.Tensor, dir: int = -1):
-        _check_tensor(x, self.numel, "input")
-        _check_tensor(out, self.numel, "output")
+        _check_tensor(x, self.numel, "input", self.dtype)
+        _check_tensor(out, self.numel, "output", self.dtype)
         s = torch.cuda.current_stream(x.device)
         _lib.obfft_exec_stage(self.handle, axis, stage, x.data_ptr(), out.data_ptr(), dir,
                               s.cuda_stream)
@@ -99,6 +108,7 @@ class PlanMany:
     def __init__(self, dims, mode="fp8"):
         self.dims = [tuple(int(v) for v in d) for d in dims]
         self.mode = _mode(mode)
+        self.dtype = dtype_of(self.mode)
         self.handle = _lib.obfft_plan_create_many(self.dims, self.mode)
 
     def exec(self, xs, outs=None, dir: int = -1, stream=None):
@@ -106,8 +116,8 @@ class PlanMany:
             outs = [torch.empty_like(x) for x in xs]
         for x, o, d in zip(xs, outs, self.dims):
             n = d[0] * d[1] * d[2]
-            _check_tensor(x, n, "input")
-            _check_tensor(o, n, "output")
+            _check_tensor(x, n, "input", self.dtype)
+            _check_tensor(o, n, "output", self.dtype)
         s = stream if stream is not None else torch.cuda.current_stream(xs[0].device)
         _lib.obfft_exec_many(self.handle, [x.data_ptr() for x in xs], [o.data_ptr() for o in outs],
                              dir, s.cuda_stream)

@@ -19,6 +19,13 @@ constexpr int CT_COLS = 32;  // columns per CTA of the INT8 stage kernel
 // Rev-34 modulus set (Background, Ozaki Scheme II paragraph).
 extern const int kModuli[NMOD];
 
+// FP32-precision variant (Sec. "Ozaki-II for FP32"): six of the Rev-34 moduli
+// (the subset with log2 M = 62.6), 8 byte slices of u_k, f = 24 (3 slices of w_k).
+constexpr int NMOD32 = 6;
+constexpr int S_RAW32 = 8;
+constexpr int S_FRAC32 = 3;
+extern const int kModuli32[NMOD32];
+
 // Per-modulus constants used on the device (one copy in __constant__ memory).
 // Offset added to the FP8 mode's reduced residues (|r| <= m/2 + 1) so that the
 // FP16 CRT operands are non-negative: r + RES_OFFSET lies in [2, 2046].
@@ -64,6 +71,8 @@ void make_mod_consts(ModConsts *mc);
 // RNE(2^52 * cos / sin(2 pi m / N)) with the sign of the imaginary part
 // chosen by dir (-1: exp(-i theta)); returns false on internal inconsistency.
 void quantised_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im);
+// The same at 2^sexp (sexp = 23: the FP32-precision variant's 24-bit significands).
+void quantised_twiddle_scaled(int64_t m, int64_t N, int dir, int sexp, int64_t *re, int64_t *im);
 
 // One axis of a grid: n = p * q.
 struct AxisPlan {
@@ -78,8 +87,9 @@ struct AxisTables {
     size_t int8_s1_bytes = 0, int8_s2_bytes = 0;
     // FP8 mode: E4M3 digit planes of the constant matrices, stage 1 / stage 2
     void *fp8_s1 = nullptr, *fp8_s2 = nullptr;
-    // FP64 native comparator: twiddles exp(dir 2 pi i m / n) for m < n as double pairs
-    double *tw = nullptr;
+    // native comparators: twiddles exp(dir 2 pi i m / n) for m < n, then the
+    // q and p tables, as double pairs (FP64) or float pairs (FP32)
+    void *tw = nullptr;
     // quantised int64 constants (kept for the FP8 path and for debugging)
     std::vector<int64_t> Fq, Fp;  // [q][q][2], [q][p][p][2]
 };
@@ -135,7 +145,16 @@ cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const vo
                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
 cudaError_t launch_stage_fp16(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
                               const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
-std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups, int K);
+std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups, int K, const int *moduli,
+                                       int nmod);
+// FP32-precision variant
+cudaError_t launch_stage_fp32(const AxisTables &t, const void *pab, int *status, const StageGeom &g, int stage,
+                              const float2 *in, float2 *out, cudaStream_t s);
+cudaError_t fp32_upload_constants();  // once per device, outside any stream capture
+size_t fp32_smem_bytes(int Kout, int npad);
+std::vector<uint8_t> build_phase_a_b32();
+cudaError_t launch_stage_native32(const AxisTables &t, const StageGeom &g, int stage, const float2 *in,
+                                  float2 *out, cudaStream_t s);
 size_t fp8_smem_bytes(int Kout, int npad);
 cudaError_t fp8_upload_constants();  // once per device, outside any stream capture
 cudaError_t launch_bounded_wait_selftest(int *status, cudaStream_t s);

@@ -27,6 +27,8 @@
 namespace obfft {
 
 const int kModuli[NMOD] = {2039, 2029, 2027, 1089, 1024, 961, 841, 625, 529, 511, 491, 487};
+// The six-member subset of the Rev-34 set with log2 M = 62.6 (Sec. "Ozaki-II for FP32").
+const int kModuli32[NMOD32] = {2039, 2029, 2027, 1024, 961, 841};
 
 static thread_local std::string g_last_error = "no error";
 
@@ -96,6 +98,23 @@ void make_mod_consts(ModConsts *mc) {
     for (int t = 0; t < S_FRAC; t++) zb += (uint64_t)0x4B000000u << (8 * t);  // mod 2^64
     mc->zbias[0] = (uint32_t)zb;
     mc->zbias[1] = (uint32_t)(zb >> 32);
+}
+
+// CRT constants of the FP32-precision variant: u_k < M < 2^63 as 8 byte
+// slices, w_k = round(2^24 u_k / M) = round(2^24 y_k / m_k) as 3 byte slices.
+static void make_crt_consts32(uint8_t us[NMOD32][S_RAW32], uint8_t ws[NMOD32][S_FRAC32], uint64_t *Mout) {
+    u128 M = 1;
+    for (int k = 0; k < NMOD32; k++) M *= (u128)kModuli32[k];
+    for (int k = 0; k < NMOD32; k++) {
+        const int64_t m = kModuli32[k];
+        const u128 Mk = M / (u128)m;
+        const int64_t y = inv_mod((int64_t)(Mk % (u128)m), m);
+        const u128 u = Mk * (u128)y;
+        for (int s = 0; s < S_RAW32; s++) us[k][s] = (uint8_t)(u >> (8 * s));
+        const u128 wk = (((u128)y << 25) + (u128)m) / ((u128)2 * (u128)m);
+        for (int t = 0; t < S_FRAC32; t++) ws[k][t] = (uint8_t)(wk >> (8 * t));
+    }
+    *Mout = (uint64_t)M;
 }
 
 // --------------------------------------------------- double-double sin / cos
@@ -172,8 +191,8 @@ static void dd_cos_sin_2pi(int64_t m, int64_t N, dd *c, dd *s) {
     }
 }
 
-static int64_t rne_dd_times_2p52(dd v) {
-    double hi = ldexp(v.hi, 52), lo = ldexp(v.lo, 52);
+static int64_t rne_dd_times_2p(dd v, int pexp) {
+    double hi = ldexp(v.hi, pexp), lo = ldexp(v.lo, pexp);
     double n = rint(hi);
     double d = (hi - n) + lo;  // hi - n exact
     if (d > 0.5) n += 1.0;
@@ -185,12 +204,15 @@ static int64_t rne_dd_times_2p52(dd v) {
     return (int64_t)n;
 }
 
-void quantised_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im) {
+void quantised_twiddle_scaled(int64_t m, int64_t N, int dir, int sexp, int64_t *re, int64_t *im) {
     dd c, s;
     dd_cos_sin_2pi(m, N, &c, &s);
-    *re = rne_dd_times_2p52(c);
-    int64_t si = rne_dd_times_2p52(s);
+    *re = rne_dd_times_2p(c, sexp);
+    int64_t si = rne_dd_times_2p(s, sexp);
     *im = dir < 0 ? -si : si;
+}
+void quantised_twiddle(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im) {
+    quantised_twiddle_scaled(m, N, dir, 52, re, im);
 }
 
 // ------------------------------------------------------------ table building
@@ -346,14 +368,15 @@ std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups,
 // FP16 values (K) in the no-swizzle K-major layout of 16-bit operands (8 x 8
 // core matrices of 16 bytes, LBO 128 between K neighbours, SBO 16 npad between
 // 8-row groups), so consecutive planes continue the rows of one operand.
-std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups, int K) {
+std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups, int K, const int *moduli,
+                                       int nmod) {
     const int npad = K <= 16 ? 16 : 32;
     const size_t planeB = (size_t)npad * npad * 2, sbo = (size_t)16 * npad;
-    std::vector<uint8_t> out((size_t)groups * FP16_PLANES_PER_GROUP * planeB, 0);
+    std::vector<uint8_t> out((size_t)groups * nmod * 8 * planeB, 0);
     size_t off = 0;
     for (int g = 0; g < groups; g++)
-        for (int k = 0; k < NMOD; k++) {
-            const int64_t m = kModuli[k];
+        for (int k = 0; k < nmod; k++) {
+            const int64_t m = moduli[k];
             for (int h = 0; h < 2; h++)
                 for (int d = 0; d < 2; d++)
                     for (int tb = 0; tb < 2; tb++) {
@@ -403,20 +426,47 @@ std::vector<uint8_t> build_phase_a_b() {
     return out;
 }
 
-static void fill_matrices(AxisTables &t) {
+// FP32 variant's Phase A B-matrix: 32 rows (Re: 8 u-slices, 3 w-slices, 5
+// zero; Im: same) x 16 K (Re residues 0..5, Im residues 6..11, 4 zero), FP16,
+// K-major canonical layout (LBO 128, SBO 256).
+std::vector<uint8_t> build_phase_a_b32() {
+    uint8_t us[NMOD32][S_RAW32], ws[NMOD32][S_FRAC32];
+    uint64_t M;
+    make_crt_consts32(us, ws, &M);
+    std::vector<uint8_t> out(32 * 32, 0);
+    for (int n = 0; n < 32; n++) {
+        const int part = n / 16, col = n % 16;
+        for (int kk = 0; kk < 16; kk++) {
+            int val = 0;
+            if (kk < 2 * NMOD32 && kk / NMOD32 == part && col < S_RAW32 + S_FRAC32) {
+                const int k = kk % NMOD32;
+                val = col < S_RAW32 ? us[k][col] : ws[k][col - S_RAW32];
+            }
+            const uint16_t h = f16_of_small(val);
+            const size_t pos = (size_t)(n / 8) * 256 + (size_t)(kk / 8) * 128 + (n % 8) * 16 + (kk % 8) * 2;
+            out[pos] = (uint8_t)(h & 0xFF);
+            out[pos + 1] = (uint8_t)(h >> 8);
+        }
+    }
+    return out;
+}
+
+// Quantised F_q and twiddle-fused F_p^(k2) at 2^sexp (52: the FP64 method, 23:
+// its FP32-precision variant).
+static void fill_matrices(AxisTables &t, int sexp) {
     const int p = t.p, q = t.q, n = t.n, dir = t.dir;
     t.Fq.assign((size_t)q * q * 2, 0);
     for (int k2 = 0; k2 < q; k2++)
         for (int j2 = 0; j2 < q; j2++)
-            quantised_twiddle((int64_t)j2 * k2 % q, q, dir, &t.Fq[((size_t)k2 * q + j2) * 2],
-                              &t.Fq[((size_t)k2 * q + j2) * 2 + 1]);
+            quantised_twiddle_scaled((int64_t)j2 * k2 % q, q, dir, sexp, &t.Fq[((size_t)k2 * q + j2) * 2],
+                                     &t.Fq[((size_t)k2 * q + j2) * 2 + 1]);
     t.Fp.assign((size_t)q * p * p * 2, 0);
     for (int k2 = 0; k2 < q; k2++)
         for (int k1 = 0; k1 < p; k1++)
             for (int j1 = 0; j1 < p; j1++) {
                 int64_t e = ((int64_t)j1 * ((int64_t)q * k1 + k2)) % n;
                 size_t idx = (((size_t)k2 * p + k1) * p + j1) * 2;
-                quantised_twiddle(e, n, dir, &t.Fp[idx], &t.Fp[idx + 1]);
+                quantised_twiddle_scaled(e, n, dir, sexp, &t.Fp[idx], &t.Fp[idx + 1]);
             }
 }
 
@@ -427,7 +477,7 @@ static cudaError_t upload(const void *host, size_t bytes, void **dev) {
 }
 
 static obfft_status build_tables(obfft_plan P, AxisTables &t) {
-    fill_matrices(t);
+    fill_matrices(t, P->mode == OBFFT_MODE_FP32 ? 23 : 52);
     cudaError_t e = cudaSuccess;
     if (P->mode == OBFFT_MODE_INT8) {
         std::vector<uint32_t> s1 = build_int8_table(t.Fq, 1, t.q);
@@ -446,10 +496,31 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
     } else if (P->mode == OBFFT_MODE_FP16) {
         e = fp8_upload_constants();
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP16 constants: ") + cudaGetErrorString(e));
-        std::vector<uint8_t> s1 = build_fp16_planes(t.Fq, 1, t.q);
-        std::vector<uint8_t> s2 = build_fp16_planes(t.Fp, t.q, t.p);
+        std::vector<uint8_t> s1 = build_fp16_planes(t.Fq, 1, t.q, kModuli, NMOD);
+        std::vector<uint8_t> s2 = build_fp16_planes(t.Fp, t.q, t.p, kModuli, NMOD);
         e = upload(s1.data(), s1.size(), &t.fp8_s1);
         if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
+    } else if (P->mode == OBFFT_MODE_FP32) {
+        e = fp32_upload_constants();
+        if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP32 constants: ") + cudaGetErrorString(e));
+        std::vector<uint8_t> s1 = build_fp16_planes(t.Fq, 1, t.q, kModuli32, NMOD32);
+        std::vector<uint8_t> s2 = build_fp16_planes(t.Fp, t.q, t.p, kModuli32, NMOD32);
+        e = upload(s1.data(), s1.size(), &t.fp8_s1);
+        if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
+    } else if (P->mode == OBFFT_MODE_FP32_NATIVE) {
+        std::vector<float> tw;
+        auto push = [&](int N) {
+            for (int m = 0; m < N; m++) {
+                dd c, s;
+                dd_cos_sin_2pi(m, N, &c, &s);
+                tw.push_back((float)c.hi);
+                tw.push_back(t.dir < 0 ? -(float)s.hi : (float)s.hi);
+            }
+        };
+        push(t.n);
+        push(t.q);
+        push(t.p);
+        e = upload(tw.data(), tw.size() * sizeof(float), &t.tw);
     } else if (P->mode == OBFFT_MODE_FP64_NATIVE) {
         std::vector<double> tw;
         auto push = [&](int N) {
@@ -463,7 +534,7 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
         push(t.n);
         push(t.q);
         push(t.p);
-        e = upload(tw.data(), tw.size() * sizeof(double), (void **)&t.tw);
+        e = upload(tw.data(), tw.size() * sizeof(double), &t.tw);
     } else {
         return set_error(OBFFT_ERR_UNSUPPORTED_SIZE, "mode not available in this build");
     }
@@ -524,8 +595,39 @@ using namespace obfft;
 // a synthetic batch of lines (stage 1 + stage 2 launches, CUDA events, best of
 // 3 after a warm-up) and keeps the fastest.  Results remain exact for the
 // chosen split; the oracle reads the split back through obfft_plan_get_splits.
-static float time_split(obfft_plan P, int n, int pp, int qq, double2 *buf, double2 *tmp, double2 *outb,
-                        int64_t lines) {
+// Bytes per complex element of the plan's data: complex128, or complex64 for
+// the FP32-precision modes.
+static size_t elem_bytes(int mode) {
+    return (mode == OBFFT_MODE_FP32 || mode == OBFFT_MODE_FP32_NATIVE) ? 8 : 16;
+}
+// Largest Bailey factor of a mode: 32 for the tcgen05 stage kernels (one
+// 128-column tile holds K <= 32), 64 otherwise.
+static int mode_kmax(int mode) {
+    return (mode == OBFFT_MODE_FP8 || mode == OBFFT_MODE_FP16 || mode == OBFFT_MODE_FP32) ? 32 : KMAX;
+}
+static bool mode_known(int mode) {
+    return mode == OBFFT_MODE_FP8 || mode == OBFFT_MODE_INT8 || mode == OBFFT_MODE_FP64_NATIVE ||
+           mode == OBFFT_MODE_FP16 || mode == OBFFT_MODE_FP32 || mode == OBFFT_MODE_FP32_NATIVE;
+}
+
+// One stage launch in the plan's mode.
+static cudaError_t launch_stage_mode(obfft_plan P, const AxisTables &t, const StageGeom &g, int stage,
+                                     const void *in, void *out, cudaStream_t s) {
+    const double2 *i2 = (const double2 *)in;
+    double2 *o2 = (double2 *)out;
+    switch (P->mode) {
+        case OBFFT_MODE_INT8: return launch_stage_int8(t, P->d_consts, g, stage, i2, o2, s);
+        case OBFFT_MODE_FP8: return launch_stage_fp8(t, P->d_consts, P->d_pab, P->d_status, g, stage, i2, o2, s);
+        case OBFFT_MODE_FP16: return launch_stage_fp16(t, P->d_consts, P->d_pab, P->d_status, g, stage, i2, o2, s);
+        case OBFFT_MODE_FP64_NATIVE: return launch_stage_fp64(t, g, stage, i2, o2, s);
+        case OBFFT_MODE_FP32:
+            return launch_stage_fp32(t, P->d_pab, P->d_status, g, stage, (const float2 *)in, (float2 *)out, s);
+        case OBFFT_MODE_FP32_NATIVE: return launch_stage_native32(t, g, stage, (const float2 *)in, (float2 *)out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static float time_split(obfft_plan P, int n, int pp, int qq, void *buf, void *tmp, void *outb, int64_t lines) {
     AxisTables t;
     t.n = n; t.p = pp; t.q = qq; t.dir = -1;
     if (build_tables(P, t) != OBFFT_OK) return 1e30f;
@@ -537,14 +639,7 @@ static float time_split(obfft_plan P, int n, int pp, int qq, double2 *buf, doubl
     float best = 1e30f;
     for (int rep = 0; rep < 4; rep++) {
         cudaEventRecord(a, 0);
-        for (int st = 1; st <= 2; st++) {
-            const double2 *src = st == 1 ? buf : tmp;
-            double2 *dst = st == 1 ? tmp : outb;
-            if (P->mode == OBFFT_MODE_INT8) launch_stage_int8(t, P->d_consts, g, st, src, dst, 0);
-            else if (P->mode == OBFFT_MODE_FP8) launch_stage_fp8(t, P->d_consts, P->d_pab, P->d_status, g, st, src, dst, 0);
-            else if (P->mode == OBFFT_MODE_FP16) launch_stage_fp16(t, P->d_consts, P->d_pab, P->d_status, g, st, src, dst, 0);
-            else launch_stage_fp64(t, g, st, src, dst, 0);
-        }
+        for (int st = 1; st <= 2; st++) launch_stage_mode(P, t, g, st, st == 1 ? buf : tmp, st == 1 ? tmp : outb, 0);
         cudaEventRecord(b, 0);
         cudaEventSynchronize(b);
         float ms = 0;
@@ -560,15 +655,15 @@ static float time_split(obfft_plan P, int n, int pp, int qq, double2 *buf, doubl
 static void autotune_splits(obfft_plan P) {
     const char *env = getenv("OBFFT_AUTOTUNE");
     if (!env || env[0] != '1') return;
-    const int kmax = (P->mode == OBFFT_MODE_FP8 || P->mode == OBFFT_MODE_FP16) ? 32 : KMAX;
+    const int kmax = mode_kmax(P->mode);
     std::map<int, std::pair<int, int>> best;
     for (auto &gd : P->grids)
         for (int a = 0; a < 3; a++) {
             const int n = (int)gd.n[a];
             if (n == 1 || best.count(n)) continue;
             const int64_t lines = std::max<int64_t>(256, ((int64_t)1 << 21) / n);
-            double2 *buf = nullptr, *tmp = nullptr, *outb = nullptr;
-            size_t bytes = (size_t)lines * n * 16;
+            void *buf = nullptr, *tmp = nullptr, *outb = nullptr;
+            size_t bytes = (size_t)lines * n * elem_bytes(P->mode);
             if (cudaMalloc(&buf, bytes) != cudaSuccess || cudaMalloc(&tmp, bytes) != cudaSuccess ||
                 cudaMalloc(&outb, bytes) != cudaSuccess) {
                 cudaFree(buf); cudaFree(tmp); cudaFree(outb);
@@ -628,7 +723,8 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
     }
     // single grid: one grid-sized scratch; several grids: one slice per grid so
     // that their launch chains do not share memory
-    P->scratch_bytes = (P->grids.size() == 1 ? maxel * (size_t)P->batch : sumel) * 16;
+    const size_t eb = elem_bytes(P->mode);
+    P->scratch_bytes = (P->grids.size() == 1 ? maxel * (size_t)P->batch : sumel) * eb;
     cudaError_t e = cudaMalloc(&P->scratch, P->scratch_bytes ? P->scratch_bytes : 16);
     if (e != cudaSuccess) {
         free_tables(P);
@@ -639,7 +735,7 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
     if (P->grids.size() > 1) {
         size_t off = 0;
         for (auto &gd : P->grids) {
-            P->grid_scratch.push_back((char *)P->scratch + off * 16);
+            P->grid_scratch.push_back((char *)P->scratch + off * eb);
             off += (size_t)(gd.n[0] * gd.n[1] * gd.n[2]);
         }
     }
@@ -648,8 +744,7 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
 }
 
 static obfft_status new_plan(int mode, obfft_plan *P) {
-    if (mode != OBFFT_MODE_FP8 && mode != OBFFT_MODE_INT8 && mode != OBFFT_MODE_FP64_NATIVE && mode != OBFFT_MODE_FP16)
-        return set_error(OBFFT_ERR_ARG, "unknown mode");
+    if (!mode_known(mode)) return set_error(OBFFT_ERR_ARG, "unknown mode");
     obfft_plan p = new obfft_plan_s();
     p->mode = mode;
     cudaGetDevice(&p->device);
@@ -657,7 +752,7 @@ static obfft_status new_plan(int mode, obfft_plan *P) {
     make_mod_consts(&mc);
     cudaError_t e = upload(&mc, sizeof(mc), (void **)&p->d_consts);
     if (e == cudaSuccess) {
-        std::vector<uint8_t> pab = build_phase_a_b();
+        std::vector<uint8_t> pab = mode == OBFFT_MODE_FP32 ? build_phase_a_b32() : build_phase_a_b();
         e = upload(pab.data(), pab.size(), &p->d_pab);
     }
     if (e == cudaSuccess) {
@@ -681,7 +776,8 @@ extern "C" obfft_status obfft_plan_create(obfft_plan *out, int64_t n0, int64_t n
     if (n0 < 1 || n1 < 1 || n2 < 1 || batch < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
     GridDesc gd;
     gd.n[0] = n0; gd.n[1] = n1; gd.n[2] = n2;
-    const int kmax = (mode == OBFFT_MODE_FP8 || mode == OBFFT_MODE_FP16) ? 32 : KMAX;
+    if (!mode_known(mode)) return set_error(OBFFT_ERR_ARG, "unknown mode");
+    const int kmax = mode_kmax(mode);
     for (int a = 0; a < 3; a++)
         if (!choose_split(gd.n[a], &gd.ax[a], kmax))
             return set_error(OBFFT_ERR_UNSUPPORTED_SIZE,
@@ -705,7 +801,7 @@ extern "C" obfft_status obfft_plan_create_many(obfft_plan *out, int count, const
         for (int a = 0; a < 3; a++) {
             gd.n[a] = dims[g * 3 + a];
             if (gd.n[a] < 1) return set_error(OBFFT_ERR_ARG, "sizes must be >= 1");
-            if (!choose_split(gd.n[a], &gd.ax[a], (mode == OBFFT_MODE_FP8 || mode == OBFFT_MODE_FP16) ? 32 : KMAX))
+            if (!choose_split(gd.n[a], &gd.ax[a], mode_kmax(mode)))
                 return set_error(OBFFT_ERR_UNSUPPORTED_SIZE, "axis length " + std::to_string(gd.n[a]) +
                                                                  " does not factor within the mode's p, q limit");
         }
@@ -759,33 +855,23 @@ static StageGeom pass_geom(const GridDesc &gd, int64_t batch, int axis) {
 }
 
 static obfft_status run_stage_geom(obfft_plan P, const AxisPlan &ap, const StageGeom &g, int stage,
-                                   const double2 *in, double2 *out, int dir, cudaStream_t s) {
+                                   const void *in, void *out, int dir, cudaStream_t s) {
     AxisTables *t = get_tables(P, ap.n, ap.p, ap.q, dir);
     if (!t) return set_error(OBFFT_ERR_INTERNAL, "missing tables");
-    cudaError_t e;
-    if (P->mode == OBFFT_MODE_INT8)
-        e = launch_stage_int8(*t, P->d_consts, g, stage, in, out, s);
-    else if (P->mode == OBFFT_MODE_FP8)
-        e = launch_stage_fp8(*t, P->d_consts, P->d_pab, P->d_status, g, stage, in, out, s);
-    else if (P->mode == OBFFT_MODE_FP16)
-        e = launch_stage_fp16(*t, P->d_consts, P->d_pab, P->d_status, g, stage, in, out, s);
-    else if (P->mode == OBFFT_MODE_FP64_NATIVE)
-        e = launch_stage_fp64(*t, g, stage, in, out, s);
-    else
-        return set_error(OBFFT_ERR_ARG, "mode not available in this build");
+    cudaError_t e = launch_stage_mode(P, *t, g, stage, in, out, s);
     if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return OBFFT_OK;
 }
 
 static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, int axis, int stage,
-                              const double2 *in, double2 *out, int dir, cudaStream_t s) {
+                              const void *in, void *out, int dir, cudaStream_t s) {
     return run_stage_geom(P, gd.ax[axis], pass_geom(gd, batch, axis), stage, in, out, dir, s);
 }
 
-static obfft_status exec_grid(obfft_plan P, const GridDesc &gd, int64_t batch, const double2 *in,
-                              double2 *out, int dir, cudaStream_t s, double2 *scratch_override = nullptr) {
-    const double2 *src = in;
-    double2 *scratch = scratch_override ? scratch_override : (double2 *)P->scratch;
+static obfft_status exec_grid(obfft_plan P, const GridDesc &gd, int64_t batch, const void *in, void *out,
+                              int dir, cudaStream_t s, void *scratch_override = nullptr) {
+    const void *src = in;
+    void *scratch = scratch_override ? scratch_override : P->scratch;
     const int64_t total = gd.n[0] * gd.n[1] * gd.n[2] * batch;
     for (int axis = 2; axis >= 0; axis--) {
         const AxisPlan &ap = gd.ax[axis];
@@ -793,7 +879,7 @@ static obfft_status exec_grid(obfft_plan P, const GridDesc &gd, int64_t batch, c
             // length-1 axis: identity; the axis rotation [B][A1][A2][1] -> [B][1][A1][A2]
             // leaves the memory order unchanged
             if (src != out) {
-                cudaError_t e = cudaMemcpyAsync(out, src, total * 16, cudaMemcpyDeviceToDevice, s);
+                cudaError_t e = cudaMemcpyAsync(out, src, total * elem_bytes(P->mode), cudaMemcpyDeviceToDevice, s);
                 if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
             }
         } else {
@@ -823,10 +909,10 @@ extern "C" obfft_status obfft_exec(obfft_plan p, const void *in, void *out, int 
     if (st != OBFFT_OK) return st;
     if (p->grids.size() != 1) return set_error(OBFFT_ERR_ARG, "plan has several grids: use obfft_exec_many");
     // the ranges must not overlap
-    size_t bytes = (size_t)(p->grids[0].n[0] * p->grids[0].n[1] * p->grids[0].n[2] * p->batch) * 16;
+    size_t bytes = (size_t)(p->grids[0].n[0] * p->grids[0].n[1] * p->grids[0].n[2] * p->batch) * elem_bytes(p->mode);
     uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
     if (a < b + bytes && b < a + bytes) return set_error(OBFFT_ERR_ARG, "in and out overlap");
-    return exec_grid(p, p->grids[0], p->batch, (const double2 *)in, (double2 *)out, dir, (cudaStream_t)stream);
+    return exec_grid(p, p->grids[0], p->batch, in, out, dir, (cudaStream_t)stream);
 }
 
 // Host-to-host execution of a one-grid plan with the copies overlapped: the
@@ -849,7 +935,8 @@ extern "C" obfft_status obfft_exec_host(obfft_plan p, const void *host_in, void 
     const GridDesc &gd = p->grids[0];
     const int64_t B = p->batch;
     const int64_t total = gd.n[0] * gd.n[1] * gd.n[2] * B;
-    const size_t bytes = (size_t)total * 16;
+    const size_t eb = elem_bytes(p->mode);
+    const size_t bytes = (size_t)total * eb;
     {
         uintptr_t a = (uintptr_t)host_in, b = (uintptr_t)host_out;
         if (a < b + bytes && b < a + bytes) return set_error(OBFFT_ERR_ARG, "host_in and host_out overlap");
@@ -862,8 +949,8 @@ extern "C" obfft_status obfft_exec_host(obfft_plan p, const void *host_in, void 
             cudaError_t e = cudaMalloc(&p->host_io[i], bytes);
             if (e != cudaSuccess) return set_error(OBFFT_ERR_ALLOC, std::string("host staging: ") + cudaGetErrorString(e));
         }
-    double2 *d0 = (double2 *)p->host_io[0], *d1 = (double2 *)p->host_io[1];
-    double2 *scr = (double2 *)p->scratch;
+    char *d0 = (char *)p->host_io[0], *d1 = (char *)p->host_io[1];
+    char *scr = (char *)p->scratch;
     // chunks: up to 16 per batch item, never fewer than 2^20 elements each
     const int64_t n2 = gd.ax[2].n, n0 = gd.ax[0].n;
     const int64_t P2 = gd.n[0] * gd.n[1], P0 = gd.n[1] * gd.n[2];
@@ -911,7 +998,7 @@ extern "C" obfft_status obfft_exec_host(obfft_plan p, const void *host_in, void 
             if (lc <= 0) continue;
             const int64_t off = (b * P2 + r0) * n2;
             cudaEvent_t ev = p->copy_events[ei++];
-            st = cuda_err(cudaMemcpyAsync(d0 + off, hin + off * 16, (size_t)lc * n2 * 16, cudaMemcpyHostToDevice,
+            st = cuda_err(cudaMemcpyAsync(d0 + off * eb, hin + off * eb, (size_t)lc * n2 * eb, cudaMemcpyHostToDevice,
                                           p->copy_stream), "input copy");
             if (st == OBFFT_OK) st = cuda_err(cudaEventRecord(ev, p->copy_stream), "event record");
             if (st == OBFFT_OK) st = cuda_err(cudaStreamWaitEvent(s, ev, 0), "stream wait");
@@ -920,8 +1007,9 @@ extern "C" obfft_status obfft_exec_host(obfft_plan p, const void *host_in, void 
             g.L = lc;
             g.P = P2;
             g.n = a2.n; g.p = a2.p; g.q = a2.q;
-            st = run_stage_geom(p, a2, g, 1, d0 + off, scr + off, dir, s);
-            if (st == OBFFT_OK) st = run_stage_geom(p, a2, g, 2, scr + off, d1 + b * n2 * P2 + r0, dir, s);
+            st = run_stage_geom(p, a2, g, 1, d0 + off * eb, scr + off * eb, dir, s);
+            if (st == OBFFT_OK)
+                st = run_stage_geom(p, a2, g, 2, scr + off * eb, d1 + (b * n2 * P2 + r0) * eb, dir, s);
             if (st != OBFFT_OK) return st;
         }
     // pass 2 (axis 1), on the device only
@@ -945,15 +1033,15 @@ extern "C" obfft_status obfft_exec_host(obfft_plan p, const void *host_in, void 
             g.P = P0;
             g.n = a0.n; g.p = a0.p; g.q = a0.q;
             const int64_t ooff = b * n0 * P0 + r0;
-            st = run_stage_geom(p, a0, g, 1, d0 + off, scr + off, dir, s);
-            if (st == OBFFT_OK) st = run_stage_geom(p, a0, g, 2, scr + off, d1 + ooff, dir, s);
+            st = run_stage_geom(p, a0, g, 1, d0 + off * eb, scr + off * eb, dir, s);
+            if (st == OBFFT_OK) st = run_stage_geom(p, a0, g, 2, scr + off * eb, d1 + ooff * eb, dir, s);
             if (st != OBFFT_OK) return st;
             cudaEvent_t ev = p->copy_events[ei++];
             st = cuda_err(cudaEventRecord(ev, s), "event record");
             if (st == OBFFT_OK) st = cuda_err(cudaStreamWaitEvent(p->copy_stream, ev, 0), "stream wait");
             if (st == OBFFT_OK)
-                st = cuda_err(cudaMemcpy2DAsync(hout + ooff * 16, (size_t)P0 * 16, d1 + ooff, (size_t)P0 * 16,
-                                                (size_t)lc * 16, (size_t)n0, cudaMemcpyDeviceToHost, p->copy_stream),
+                st = cuda_err(cudaMemcpy2DAsync(hout + ooff * eb, (size_t)P0 * eb, d1 + ooff * eb, (size_t)P0 * eb,
+                                                (size_t)lc * eb, (size_t)n0, cudaMemcpyDeviceToHost, p->copy_stream),
                               "output copy");
             if (st != OBFFT_OK) return st;
         }
@@ -994,8 +1082,7 @@ extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, vo
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
         obfft_status st = OBFFT_OK;
         for (size_t g = 0; g < G && st == OBFFT_OK; g++)
-            st = exec_grid(p, p->grids[g], 1, (const double2 *)ins[g], (double2 *)outs[g], dir, p->capture_stream,
-                           (double2 *)p->grid_scratch[g]);
+            st = exec_grid(p, p->grids[g], 1, ins[g], outs[g], dir, p->capture_stream, p->grid_scratch[g]);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(p->capture_stream, &graph);
         if (st != OBFFT_OK) {
@@ -1025,8 +1112,7 @@ extern "C" obfft_status obfft_exec_stage(obfft_plan p, int axis, int stage, cons
     obfft_status st = check_ptrs(in, out);
     if (st != OBFFT_OK) return st;
     if (p->grids[0].ax[axis].n == 1) return set_error(OBFFT_ERR_ARG, "axis of length 1 has no stages");
-    st = run_stage(p, p->grids[0], p->batch, axis, stage, (const double2 *)in, (double2 *)out, dir,
-                   (cudaStream_t)stream);
+    st = run_stage(p, p->grids[0], p->batch, axis, stage, in, out, dir, (cudaStream_t)stream);
     return st;
 }
 
@@ -1067,6 +1153,25 @@ extern "C" obfft_status obfft_host_crt_constants(uint32_t *moduli, uint8_t *u_sl
         for (int t = 0; t < S_FRAC; t++) w_slices[k * S_FRAC + t] = mc.ws[k][t];
     }
     for (int w = 0; w < 4; w++) M4[w] = mc.M32[w];
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_host_twiddle32(int64_t m, int64_t N, int dir, int64_t *re, int64_t *im) {
+    if (N < 1 || !re || !im) return set_error(OBFFT_ERR_ARG, "bad argument");
+    quantised_twiddle_scaled(m, N, dir, 23, re, im);
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_host_crt_constants32(uint32_t *moduli, uint8_t *u_slices, uint8_t *w_slices,
+                                                   uint64_t *M) {
+    if (!moduli || !u_slices || !w_slices || !M) return set_error(OBFFT_ERR_ARG, "NULL output");
+    uint8_t us[NMOD32][S_RAW32], ws[NMOD32][S_FRAC32];
+    make_crt_consts32(us, ws, M);
+    for (int k = 0; k < NMOD32; k++) {
+        moduli[k] = (uint32_t)kModuli32[k];
+        for (int s = 0; s < S_RAW32; s++) u_slices[k * S_RAW32 + s] = us[k][s];
+        for (int t = 0; t < S_FRAC32; t++) w_slices[k * S_FRAC32 + t] = ws[k][t];
+    }
     return OBFFT_OK;
 }
 

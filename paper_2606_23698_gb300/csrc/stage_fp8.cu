@@ -46,6 +46,7 @@
 #include "device_common.cuh"
 #include "obfft_internal.h"
 #include "tc_common.cuh"
+#include "tc_stage.cuh"
 
 namespace obfft {
 
@@ -69,49 +70,12 @@ constexpr int PA_N = 48;          // Phase A output columns (Re 24 | Im 24)
 constexpr int PA_ROWB = 384;      // bytes per 8-row group of the staging (3 K-chunks)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
-struct ColMapT {
-    int stage;
-    int64_t L, Lpad, P;
-    int n, p, q;
-    __device__ __forceinline__ bool valid(int64_t c, int64_t ncols) const {
-        if (c >= ncols) return false;
-        if (stage == 2) return (c % Lpad) < L;
-        return true;
-    }
-    __device__ __forceinline__ int group(int64_t c) const { return stage == 1 ? 0 : (int)(c / Lpad); }
-    // element j of column c lives at ibase + j * istride; output k at obase + k * ostride
-    __device__ __forceinline__ void strides(int64_t c, int64_t &ibase, int64_t &istride, int64_t &obase,
-                                            int64_t &ostride) const {
-        if (stage == 1) {
-            int64_t l = c / p, j1 = c - l * p;
-            ibase = l * n + j1;
-            istride = p;
-            obase = ibase;
-            ostride = p;
-        } else {
-            int64_t k2 = c / Lpad, l = c - k2 * Lpad;
-            int64_t b = l / P, r = l - b * P;
-            ibase = l * n + k2 * p;
-            istride = 1;
-            obase = (b * n + k2) * P + r;
-            ostride = (int64_t)q * P;
-        }
-    }
-};
 
 // byte offset of element (row, k) of the Phase-A staging (K-major, 3 chunks of 8 f16)
 __device__ __forceinline__ uint32_t stage_off(uint32_t row, uint32_t k) {
     return (row >> 3) * PA_ROWB + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// Reduced residue plus RES_OFFSET of two exact integers |x| < 2^24 (packed):
-// q = RNE(x / m) from the rounded reciprocal is within one of the true
-// quotient, so x - m q lies in [-m/2 - 1, m/2 + 1] and the offset value in
-// [2, 2046]: exact in FP16, non-negative for the biased Phase-A deposits.
-__device__ __forceinline__ float2 offset_residue2(float2 x, float2 nm, float2 im) {
-    const float2 q = rint2_mul(x, im);
-    return __fadd2_rn(__ffma2_rn(nm, q, x), f2splat((float)RES_OFFSET));
-}
 
 // ---------------------------------------------------------------------------
 // Kernel: 512 threads.  Thread (sub = warp % 4, qd = warp / 4) owns TMEM lane
@@ -210,20 +174,6 @@ __device__ __forceinline__ void issue_modulus_nm(uint32_t dacc, uint32_t apl, ui
     }
 }
 
-// FP16 carrier: per half (x_R, x_I) and K chunk of 16 elements one
-// tcgen05.mma kind::f16 (M = 128, N = 4 npad: digit c0 then c1, Re and Im rows
-// side by side, K = 16) into the two class accumulators (class 1 at 2 npad).
-template <int NPAD>
-__device__ __forceinline__ void issue_modulus_f16(uint32_t dacc, uint32_t apl, uint64_t bdesc) {
-    constexpr uint32_t planeB16 = NPAD * NPAD * 2 / 16;  // plane size in 16-byte descriptor units
-#pragma unroll
-    for (int h = 0; h < 2; h++)
-#pragma unroll
-        for (int kc = 0; kc < NPAD / 16; kc++)
-            tc_mma_f16_ta(dacc, apl + (uint32_t)(h * NPAD / 2 + kc * 8),
-                          bdesc + (uint64_t)(h * 4) * planeB16 + (uint64_t)(kc * 16), instr_desc(128, 4 * NPAD, 0),
-                          (h == 0 && kc == 0) ? 0u : 1u);
-}
 
 constexpr int fp8_ncls_of_kind(int kind) {
     return kind == KIND_B11 ? 5 : ((kind == KIND_SQ || kind == KIND_F16) ? 2 : 3);

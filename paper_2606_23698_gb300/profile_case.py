@@ -22,14 +22,14 @@ def main(argv):
     shape = tuple(int(v) for v in argv[1:4])
     if what == "stage":
         axis, stage, mode = int(argv[4]), int(argv[5]), argv[6]
-        x = S.complex_uniform(1, shape, device="cuda")
         pl = Plan(*shape, mode=mode)
+        x = S.complex_uniform(1, shape, device="cuda").to(pl.dtype)
         out = torch.empty_like(x)
         pl.exec_stage(axis, stage, x, out)
     elif what == "fft3":
         mode = argv[4]
-        x = S.complex_uniform(1, shape, device="cuda")
         pl = Plan(*shape, mode=mode)
+        x = S.complex_uniform(1, shape, device="cuda").to(pl.dtype)
         out = torch.empty_like(x)
         pl.exec(x, out)
     else:

@@ -71,3 +71,25 @@ def test_host_constants_match_oracle(lib):
     assert [list(us[15 * k:15 * k + 15]) for k in range(12)] == C.U_SLICES
     assert [list(ws[6 * k:6 * k + 6]) for k in range(12)] == C.W_SLICES
     assert sum(int(M4[i]) << (32 * i) for i in range(4)) == C.M
+
+
+def test_host_constants_fp32_variant_match_oracle(lib):
+    """FP32-precision variant: RNE(2^23 omega), the six moduli, their u_k / w_k
+    slices and M from the library agree with the oracle's definitions."""
+    from oracle import constants as C
+    re_, im_ = ctypes.c_int64(), ctypes.c_int64()
+    for N in (8, 12, 16, 32, 96, 1024):
+        for m in range(0, N, max(1, N // 61)):
+            for d in (-1, 1):
+                assert lib.obfft_host_twiddle32(m, N, d, ctypes.byref(re_), ctypes.byref(im_)) == 0
+                assert (re_.value, im_.value) == C.quantised_twiddle(m, N, d, C.SIGMA_F_EXP_FP32), (m, N, d)
+    mods = (ctypes.c_uint32 * 6)()
+    us = (ctypes.c_uint8 * 48)()
+    ws = (ctypes.c_uint8 * 18)()
+    M = ctypes.c_uint64()
+    assert lib.obfft_host_crt_constants32(mods, us, ws, ctypes.byref(M)) == 0
+    assert list(mods) == list(C.MODULI_FP32)
+    assert [list(us[8 * k:8 * k + 8]) for k in range(6)] == C.U_SLICES_FP32
+    assert [list(ws[3 * k:3 * k + 3]) for k in range(6)] == C.W_SLICES_FP32
+    assert M.value == C.M_FP32
+    assert lib.obfft_host_crt_constants32(None, us, ws, ctypes.byref(M)) == 1

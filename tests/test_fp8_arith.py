@@ -98,3 +98,26 @@ def test_offset_lifts_to_c_plus_offset():
         e = sum(ri * ui for ri, ui in zip(r, us)) % M
         e = e - M if e >= M // 2 else e
         assert e == c + 1024
+
+
+# --------------------------------------------------------------------------
+# FP32-precision variant: data residues of the exact integers |x~| < 2^24
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [int(v) for v in C.MODULI_FP32])
+def test_fp32_variant_balanced_residue_exhaustive(m):
+    """v1 = x - m RNE(x fl(1/m)), v = v1 - m RNE(v1 fl(1/m)) (RNE of the exact
+    products, as the fused magic-number rounding computes them) is the balanced
+    residue |v| <= m/2, v = x (mod m), for every integer |x| < 2^24."""
+    f = float(np.float32(1.0 / m))                 # the kernel's rounded reciprocal
+    step = 1 << 20
+    for lo in range(-(1 << 24) + 1, 1 << 24, step):
+        x = np.arange(lo, min(lo + step, 1 << 24), dtype=np.float64)
+        q1 = np.rint(x * f)                           # x f is exact in float64 (24 x 24 bits)
+        assert np.all(np.abs(x * f) < 2 ** 22)        # range of the magic-number rounding
+        v1 = x - m * q1
+        q2 = np.rint(v1 * f)
+        v = v1 - m * q2
+        assert np.all(2 * np.abs(v) <= m)
+        assert np.all(np.mod(v - x, m) == 0)
+    # FP16 carrier bound for the largest modulus
+    assert m // 2 <= 1020
