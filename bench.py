@@ -190,7 +190,24 @@ def fp32_variant(torch, Plan, x, y64, stream):
                 pl.exec_stage(2, 1, x32, scratch)
             k1.record(stream)
             torch.cuda.synchronize()
-            res["stage_kernel_ms"] = k0.elapsed_time(k1) / 3
+            kms = k0.elapsed_time(k1) / 3
+            res["stage_kernel_ms"] = kms
+            # the paper's FP32 epilogue model: c_epi = 109-152 integer instructions
+            # per output scalar (hardware-ladder section, FP32 paragraph); 2 scalars
+            # per complex element and stage launch
+            N3 = x.numel()
+            peaks = measured_peaks()
+            alu_peak = 152 * 4 * 32 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            ach = 2 * 109 * N3 / (kms * 1e-3) / 1e12
+            res["roofline"] = {
+                "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tinst/s", "frac": ach / alu_peak,
+                "kernel": "stage_fp32_kernel (axis 2, stage 1)",
+                "algorithmic": "218 integer instructions per complex output (paper c_epi = 109 per scalar)",
+                "hbm_frac_of_measured": (16 * N3 / (kms * 1e-3) / 1e9) / peaks.get("hbm_gbs", 6791.0),
+                # one ncu capture of the same kernel on 16 x 1024 x 1024 complex64
+                # (128 MiB in and out): dram read 134,478,592 + write 91,217,152 bytes,
+                # scaled by the 64 times more columns of a 1024^3 launch
+                "traffic": (134478592 + 91217152) * 64 if N3 == 1024 ** 3 else None}
             del scratch
         out[m] = res
         pl.close()
