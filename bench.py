@@ -424,6 +424,13 @@ def main():
         fp32 = fp32_variant(torch, Plan, x, y64_keep, stream)
     del y64_keep
 
+    # epilogue ablation: Kulisch word widths and deconstruction residue forms,
+    # stand-alone kernels over L2-resident synthetic inputs
+    ablation = None
+    if rank == 0 and not args.no_extra:
+        from paper_2606_23698_gb300.ablation import measure
+        ablation = measure()
+
     extra = None
     if not args.no_extra and rank == 0 and n == 1024:
         del y_main
@@ -479,7 +486,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "gflops_5nlogn": gflops, "modes_ms": modes, "rel_diff_vs_fp64_native": diff,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches, "side_configs": extra, "fp32_variant": fp32}
+            "gpu_launches": launches, "side_configs": extra, "fp32_variant": fp32,
+            "epilogue_ablation": ablation}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

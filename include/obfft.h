@@ -199,6 +199,38 @@ obfft_status obfft_host_twiddle32(int64_t m, int64_t N, int dir, int64_t *re, in
 obfft_status obfft_host_crt_constants32(uint32_t *moduli, uint8_t *u_slices, uint8_t *w_slices, uint64_t *M);
 
 /*
+ * Epilogue ablation (the paper's width-parameterised Kulisch accumulator,
+ * Sec. "The accumulator is substrate-agnostic", Sec. "INT16 and INT8",
+ * Eq. kulisch-width; and the dp4a migration of the deconstruction bulk,
+ * Sec. "Deconstruction count").  Exact alternative forms of two epilogue
+ * parts, run stand-alone on device buffers so that their instruction mix and
+ * throughput can be measured; every variant gives bit-identical results.
+ *
+ * obfft_ablation_phase_b: Phase B (Kulisch sum, two-sided lift, correctly
+ * rounded pack) of scalar outputs.  acc: device uint32 [n_unique][21], the
+ * Phase-A accumulators of one output as FP32 bit patterns 2^23 + P_s (s < 15)
+ * then 2^23 + Q_t (t < 6), of offset residues r_k + 1024 (P_s, Q_t < 2^23);
+ * et: device int32 [n_unique], the output is RNE(C 2^et) where C is the value
+ * the residues encode.  variant: 0 = the stage kernels' path (four 64-bit
+ * partial sums), 32 / 16 / 8 = deposits into words of that width (radix 2^28,
+ * 2^12, 2^6), packed 32 / variant per register.
+ * obfft_ablation_residues: canonical residues x~ mod m_k of the 12 moduli.
+ * xt: device int64 [n_unique], |x~| < 2^53; variant 0 = the stage kernels'
+ * 20/20/16-bit pieces with Barrett, 1 = dp4a over the bytes of x~ + 2^55,
+ * 2 = 64-bit remainder.
+ * Both: item i < n_total uses input i mod n_unique; the results of the first
+ * n_unique items go to out (double [n_unique]) / res (uint16 [n_unique][12])
+ * when those are non-NULL; *checksum (device uint64, caller-initialised) is
+ * XOR-combined with a hash of every result.  Asynchronous on `stream`.
+ * OBFFT_ERR_ARG for an unknown variant, n_unique < 1, n_total < 0 or NULL
+ * inputs.
+ */
+obfft_status obfft_ablation_phase_b(int variant, int64_t n_unique, int64_t n_total, const void *acc,
+                                    const void *et, void *out, void *checksum, void *stream);
+obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_total, const void *xt, void *res,
+                                     void *checksum, void *stream);
+
+/*
  * Largest grid (n0 * n1 * n2 complex128 values) obfft_exec_fp64_noalloc accepts.
  */
 #define OBFFT_NOALLOC_MAX_ELEMS (1 << 21)

@@ -37,7 +37,8 @@ EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_s
            "obfft_plan_create_many", "obfft_exec_many", "obfft_exec_stage", "obfft_last_error",
            "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants",
            "obfft_exec_fp64_noalloc", "obfft_plan_status", "obfft_selftest_bounded_wait",
-           "obfft_exec_host", "obfft_host_twiddle32", "obfft_host_crt_constants32")
+           "obfft_exec_host", "obfft_host_twiddle32", "obfft_host_crt_constants32",
+           "obfft_ablation_phase_b", "obfft_ablation_residues")
 
 _lib = None
 
@@ -86,6 +87,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_selftest_bounded_wait.restype = i32
     L.obfft_exec_fp64_noalloc.argtypes = [vp, vp, i64, i64, i64, i32, vp]
     L.obfft_exec_fp64_noalloc.restype = i32
+    L.obfft_ablation_phase_b.argtypes = [i32, i64, i64, vp, vp, vp, vp, vp]
+    L.obfft_ablation_phase_b.restype = i32
+    L.obfft_ablation_residues.argtypes = [i32, i64, i64, vp, vp, vp, vp]
+    L.obfft_ablation_residues.restype = i32
     _lib = L
     return L
 
@@ -171,6 +176,18 @@ def obfft_host_crt_constants32():
     check(load().obfft_host_crt_constants32(mod, us, ws, ctypes.byref(M)))
     return list(mod), [list(us[8 * k:8 * k + 8]) for k in range(6)], \
         [list(ws[3 * k:3 * k + 3]) for k in range(6)], M.value
+
+
+def obfft_ablation_phase_b(variant: int, n_unique: int, n_total: int, acc_ptr: int, et_ptr: int,
+                           out_ptr: int | None, checksum_ptr: int, stream: int = 0) -> None:
+    """Phase B of n_total scalar outputs in one accumulator layout (device pointers)."""
+    check(load().obfft_ablation_phase_b(variant, n_unique, n_total, acc_ptr, et_ptr, out_ptr, checksum_ptr, stream))
+
+
+def obfft_ablation_residues(variant: int, n_unique: int, n_total: int, xt_ptr: int, res_ptr: int | None,
+                            checksum_ptr: int, stream: int = 0) -> None:
+    """Residues of n_total deconstructed integers in one instruction form (device pointers)."""
+    check(load().obfft_ablation_residues(variant, n_unique, n_total, xt_ptr, res_ptr, checksum_ptr, stream))
 
 
 def obfft_last_error() -> str:

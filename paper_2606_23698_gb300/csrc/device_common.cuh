@@ -273,40 +273,20 @@ __device__ __forceinline__ double kulisch_pack_fp8(const uint32_t *wv, const Mod
     return __longlong_as_double((long long)bits);
 }
 
-// Straight-line form of the common case of kulisch_pack_fp8, for two outputs
-// computed side by side: no early exits, so the compiler can interleave the
-// chains.  Sets `slow` (and returns an unspecified value) when the general
-// finish is needed: lift near a rounding boundary, |R| < 2^64, or a result
-// that is subnormal or overflows; Rw (R = E - bias - zhat M mod 2^128) and
-// near_out then feed kulisch_finish_general.  Otherwise the result equals
-// kulisch_pack_fp8's bit for bit.
-__device__ __forceinline__ double kulisch_pack_fp8_fast(const uint32_t *wv, const ModConsts &mc, int et,
-                                                        const uint32_t (&ebias)[4], uint64_t zbias, bool &slow,
-                                                        uint32_t (&Rw)[4], bool &near_out) {
-    uint64_t a0 = (uint64_t)wv[0];
-    a0 += (uint64_t)wv[1] * 256u;
-    a0 += (uint64_t)wv[2] * 65536u;
-    a0 += (uint64_t)wv[3] * 16777216u;
-    uint64_t a1 = (uint64_t)wv[4];
-    a1 += (uint64_t)wv[5] * 256u;
-    a1 += (uint64_t)wv[6] * 65536u;
-    a1 += (uint64_t)wv[7] * 16777216u;
-    uint64_t a2 = (uint64_t)wv[8];
-    a2 += (uint64_t)wv[9] * 256u;
-    a2 += (uint64_t)wv[10] * 65536u;
-    a2 += (uint64_t)wv[11] * 16777216u;
-    uint64_t a3 = (uint64_t)wv[12];
-    a3 += (uint64_t)wv[13] * 256u;
-    a3 += (uint64_t)wv[14] * 65536u;
-    const uint32_t w0 = (uint32_t)a0;
-    uint64_t t = (a0 >> 32) + a1;
-    const uint32_t w1 = (uint32_t)t;
-    t = (t >> 32) + a2;
-    const uint32_t w2 = (uint32_t)t;
-    t = (t >> 32) + a3;
-    const uint32_t w3 = (uint32_t)t;
-    uint64_t z = (uint64_t)wv[15] + (uint64_t)wv[16] * 256u + (uint64_t)wv[17] * 65536u +
-                 (uint64_t)wv[18] * 16777216u + ((uint64_t)wv[19] << 32) + ((uint64_t)wv[20] << 40);
+// Straight-line lift and pack of the common case of kulisch_pack_fp8, from the
+// words w0..w3 of the deposited sum (mod 2^128), the six w_k partials wq (FP32
+// bit patterns 2^23 + Q_t) and the constant `ebias` to remove (deposit biases
+// and the residue offset): no early exits, so the compiler can interleave two
+// outputs' chains.  Sets `slow` (and returns an unspecified value) when the
+// general finish is needed: lift near a rounding boundary, |R| < 2^64, or a
+// result that is subnormal or overflows; Rw (R = E - ebias - zhat M mod 2^128)
+// and near_out then feed kulisch_finish_general.
+__device__ __forceinline__ double lift_pack_fast(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                                 const uint32_t *wq, const ModConsts &mc, int et,
+                                                 const uint32_t (&ebias)[4], uint64_t zbias, bool &slow,
+                                                 uint32_t (&Rw)[4], bool &near_out) {
+    uint64_t z = (uint64_t)wq[0] + (uint64_t)wq[1] * 256u + (uint64_t)wq[2] * 65536u +
+                 (uint64_t)wq[3] * 16777216u + ((uint64_t)wq[4] << 32) + ((uint64_t)wq[5] << 40);
     z -= zbias;
     const uint64_t zr = z + (1ull << 47);
     const uint32_t zhat = (uint32_t)(zr >> 48);
@@ -353,6 +333,38 @@ __device__ __forceinline__ double kulisch_pack_fp8_fast(const uint32_t *wv, cons
     slow = near || hi == 0 || E2 < 1 || E2 > 2046;
     const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)(uint32_t)E2 << 52) | (mant & ((1ull << 52) - 1));
     return __longlong_as_double((long long)bits);
+}
+
+// Straight-line form of the common case of kulisch_pack_fp8: the deposits of
+// the 15 slices in four 64-bit partial sums of four slices each (Eq. accwidth's
+// grouping), assembled into 128-bit words, then lift_pack_fast.  Otherwise the
+// result equals kulisch_pack_fp8's bit for bit.
+__device__ __forceinline__ double kulisch_pack_fp8_fast(const uint32_t *wv, const ModConsts &mc, int et,
+                                                        const uint32_t (&ebias)[4], uint64_t zbias, bool &slow,
+                                                        uint32_t (&Rw)[4], bool &near_out) {
+    uint64_t a0 = (uint64_t)wv[0];
+    a0 += (uint64_t)wv[1] * 256u;
+    a0 += (uint64_t)wv[2] * 65536u;
+    a0 += (uint64_t)wv[3] * 16777216u;
+    uint64_t a1 = (uint64_t)wv[4];
+    a1 += (uint64_t)wv[5] * 256u;
+    a1 += (uint64_t)wv[6] * 65536u;
+    a1 += (uint64_t)wv[7] * 16777216u;
+    uint64_t a2 = (uint64_t)wv[8];
+    a2 += (uint64_t)wv[9] * 256u;
+    a2 += (uint64_t)wv[10] * 65536u;
+    a2 += (uint64_t)wv[11] * 16777216u;
+    uint64_t a3 = (uint64_t)wv[12];
+    a3 += (uint64_t)wv[13] * 256u;
+    a3 += (uint64_t)wv[14] * 65536u;
+    const uint32_t w0 = (uint32_t)a0;
+    uint64_t t = (a0 >> 32) + a1;
+    const uint32_t w1 = (uint32_t)t;
+    t = (t >> 32) + a2;
+    const uint32_t w2 = (uint32_t)t;
+    t = (t >> 32) + a3;
+    const uint32_t w3 = (uint32_t)t;
+    return lift_pack_fast(w0, w1, w2, w3, wv + 15, mc, et, ebias, zbias, slow, Rw, near_out);
 }
 
 // General finish from R = E - bias - zhat M (mod 2^128): the two-sided

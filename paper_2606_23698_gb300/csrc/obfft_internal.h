@@ -64,6 +64,11 @@ struct ModConsts {
     // sum_{t<6} 0x4B000000 * 256^t mod 2^64
     uint32_t kbias[4];
     uint32_t zbias[2];
+    // dp4a form of the deconstruction (epilogue ablation): the bytes of
+    // 2^(8i) mod m, i < 7, low 8 bits (b8lo) and bits 8..10 (b8hi), packed four
+    // per word: [0] = i 0..3, [1] = i 4..6
+    uint32_t b8lo[NMOD][2];
+    uint32_t b8hi[NMOD][2];
 };
 
 // Host-side constant generation (plan.cpp).
@@ -160,6 +165,11 @@ cudaError_t fp8_upload_constants();  // once per device, outside any stream capt
 cudaError_t launch_bounded_wait_selftest(int *status, cudaStream_t s);
 std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K);
 std::vector<uint8_t> build_phase_a_b();
+// Epilogue ablation kernels (ablation.cu)
+cudaError_t launch_phase_b_ablation(int variant, int64_t n_unique, int64_t n_total, const uint32_t *acc,
+                                    const int *et, double *out, unsigned long long *checksum, cudaStream_t s);
+cudaError_t launch_residue_ablation(int variant, int64_t n_unique, int64_t n_total, const int64_t *xt,
+                                    uint16_t *res, unsigned long long *checksum, cudaStream_t s);
 cudaError_t launch_stage_fp64(const AxisTables &t, const StageGeom &g, int stage,
                               const double2 *in, double2 *out, cudaStream_t s);
 }  // namespace obfft

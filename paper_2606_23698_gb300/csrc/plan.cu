@@ -85,6 +85,11 @@ void make_mod_consts(ModConsts *mc) {
         mc->fsq[k] = (float)sq;
         mc->fc3[k] = (float)(4096 % m);
         mc->fc4[k] = (float)(65536 % m);
+        for (int i = 0; i < 7; i++) {
+            const uint32_t c = (uint32_t)pow2_mod(8 * i, m);  // < 2^11
+            mc->b8lo[k][i / 4] |= (c & 0xFFu) << (8 * (i % 4));
+            mc->b8hi[k][i / 4] |= (c >> 8) << (8 * (i % 4));
+        }
     }
     for (int w = 0; w < 4; w++) {
         mc->M32[w] = (uint32_t)(M >> (32 * w));
@@ -1173,6 +1178,25 @@ extern "C" obfft_status obfft_host_crt_constants32(uint32_t *moduli, uint8_t *u_
         for (int t = 0; t < S_FRAC32; t++) w_slices[k * S_FRAC32 + t] = ws[k][t];
     }
     return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_ablation_phase_b(int variant, int64_t n_unique, int64_t n_total, const void *acc,
+                                              const void *et, void *out, void *checksum, void *stream) {
+    if (variant != 0 && variant != 32 && variant != 16 && variant != 8)
+        return set_error(OBFFT_ERR_ARG, "variant must be 0, 32, 16 or 8");
+    if (n_unique < 1 || n_total < 0 || !acc || !et || !checksum) return set_error(OBFFT_ERR_ARG, "bad argument");
+    cudaError_t e = launch_phase_b_ablation(variant, n_unique, n_total, (const uint32_t *)acc, (const int *)et,
+                                            (double *)out, (unsigned long long *)checksum, (cudaStream_t)stream);
+    return e == cudaSuccess ? OBFFT_OK : set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_total, const void *xt,
+                                               void *res, void *checksum, void *stream) {
+    if (variant < 0 || variant > 2) return set_error(OBFFT_ERR_ARG, "variant must be 0, 1 or 2");
+    if (n_unique < 1 || n_total < 0 || !xt || !checksum) return set_error(OBFFT_ERR_ARG, "bad argument");
+    cudaError_t e = launch_residue_ablation(variant, n_unique, n_total, (const int64_t *)xt, (uint16_t *)res,
+                                            (unsigned long long *)checksum, (cudaStream_t)stream);
+    return e == cudaSuccess ? OBFFT_OK : set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
 }
 
 extern "C" const char *obfft_last_error(void) { return g_last_error.c_str(); }

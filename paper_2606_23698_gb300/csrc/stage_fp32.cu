@@ -196,10 +196,11 @@ __device__ __forceinline__ void prefetch_input_tile32(const ColMapT &map, const 
 // Kernel.  Thread (sub = warp % 4, qd = warp / 4) owns TMEM lane c = 32 sub +
 // lane (DFT column c of the tile), deconstructs elements [EPT qd, EPT qd +
 // EPT) of that column and finishes outputs [OPT qd, OPT qd + OPT).
-// TMEM (256 columns): class accumulators [0, 4 npad) (class cl, Re at
-// 2 cl npad, Im npad later); FP16 A buffers of the data residues at 4 npad +
-// b npad (x_R in the first npad / 2 columns, x_I in the next); Phase A reuses
-// [0, 8 x 32).
+// TMEM (512 columns): two sets of class accumulators, set b at [4 b npad,
+// 4 (b + 1) npad) (class cl, Re at 2 cl npad, Im npad later), so that the MMAs
+// of modulus k+1 run while the epilogue of modulus k reads its set; FP16 A
+// buffers of the data residues at 8 npad + b npad (x_R in the first npad / 2
+// columns, x_I in the next); Phase A reuses [0, 8 x 32).
 // ---------------------------------------------------------------------------
 template <int NPAD>
 __global__ void __launch_bounds__(F32_WARPS * 32, 1)
@@ -208,14 +209,15 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
                       int *status, int pf_ahead, int tma_in) {
     constexpr int EPT = NPAD / 4, OPT = NPAD / 4;
     constexpr uint32_t PLANE_B = NPAD * NPAD * 2, BUF_PLANES = 8, SBO = 16 * NPAD;
-    constexpr uint32_t APL = 4 * NPAD;  // first A buffer
+    constexpr uint32_t ACC = 4 * NPAD;  // columns of one accumulator set (two classes, Re | Im)
+    constexpr uint32_t APL = 2 * ACC;   // first A buffer, after the two accumulator sets
     extern __shared__ __align__(1024) uint8_t smem[];
     const ModConsts32 &mc = c_fp32_mc;
     __shared__ int colpart[4][128];
-    // 0,1: B planes (TMA, per buffer), 2: MMA, 3: Phase-A B, 4: input tile
-    __shared__ __align__(8) uint64_t mbar[5];
+    // 0,1: B planes (TMA, per buffer), 2,3: MMAs of modulus k (per accumulator
+    // set k & 1), 4: Phase-A B, 5: input tile, 6: Phase-A MMAs
+    __shared__ __align__(8) uint64_t mbar[7];
     __shared__ uint32_t tmem_holder;
-    __shared__ int abort_flag;
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int sub = w & 3, qd = w >> 2;
@@ -235,20 +237,19 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     __shared__ int64_t s_e0;
 
     if (w == 0) {
-        tmem_alloc(smem_u32(&tmem_holder), 256);
+        tmem_alloc(smem_u32(&tmem_holder), 512);
     } else if (w == 1) {
         const InputTile32 itile = input_tile32(map, ncols, cbase);
         if (lane == 0) {
-            abort_flag = 0;
             s_e0 = itile.e0;
-            for (int b = 0; b < 5; b++) mbar_init(smem_u32(&mbar[b]), 1);
+            for (int b = 0; b < 7; b++) mbar_init(smem_u32(&mbar[b]), 1);
             mbar_fence_init();
         }
         __syncwarp();
-        if (tma_in) copy_input_tile32(map, itile, K, in, sIn, smem_u32(&mbar[4]), lane);
+        if (tma_in) copy_input_tile32(map, itile, K, in, sIn, smem_u32(&mbar[5]), lane);
         if (lane == 0) {
-            mbar_expect_tx(smem_u32(&mbar[3]), PA32_N * 32);
-            tma_bulk_g2s(smem_u32(sPAB), pab, PA32_N * 32, smem_u32(&mbar[3]));
+            mbar_expect_tx(smem_u32(&mbar[4]), PA32_N * 32);
+            tma_bulk_g2s(smem_u32(sPAB), pab, PA32_N * 32, smem_u32(&mbar[4]));
             mbar_expect_tx(smem_u32(&mbar[0]), BUF_PLANES * PLANE_B);
             tma_bulk_g2s(smem_u32(sB0), gplanes, BUF_PLANES * PLANE_B, smem_u32(&mbar[0]));
         }
@@ -266,14 +267,15 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         __syncthreads();
     }
 
+    bool bad = false;  // this thread saw a bounded wait give up
     // ---------------- deconstruction of this thread's EPT elements ----------------
     float2 xt[EPT];
     int e;
     int64_t ibase, istride, obase, ostride;
     map.strides(cg, ibase, istride, obase, ostride);
     {
-        const bool okin = tma_in ? mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT32) : true;
-        if (!okin) atomicExch(&abort_flag, 1);
+        const bool okin = tma_in ? mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT32) : true;
+        if (!okin) bad = true;
         const int64_t sbase = map.stage == 1 ? ibase - s_e0 : (int64_t)c * (K + 2);
         const int64_t sstride = map.stage == 1 ? istride : 1;
         float2 x[EPT];
@@ -322,8 +324,9 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     };
     auto issue = [&](int k) -> bool {
         if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT32)) return false;
-        issue_modulus_f16<NPAD>(tmem, tmem + APL + (uint32_t)(k & 1) * NPAD, (k & 1) ? bdesc1 : bdesc0);
-        tc_commit(smem_u32(&mbar[2]));
+        issue_modulus_f16<NPAD>(tmem + (uint32_t)(k & 1) * ACC, tmem + APL + (uint32_t)(k & 1) * NPAD,
+                                (k & 1) ? bdesc1 : bdesc0);
+        tc_commit(smem_u32(&mbar[2 + (k & 1)]));
         return true;
     };
     // Epilogue of modulus k: both classes of the Re and Im products of this
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         const float2 nm2 = f2splat(-mc.fm[k]), im2 = f2splat(mc.finv[k]);
 #pragma unroll
         for (int part = 0; part < 2; part++) {
-            const uint32_t ta = tmem + lanebase + (uint32_t)(part * NPAD + qd * OPT);
+            const uint32_t ta = tmem + lanebase + (uint32_t)(k & 1) * ACC + (uint32_t)(part * NPAD + qd * OPT);
             uint32_t r0[OPT], r1[OPT];
             if constexpr (OPT == 8) {
                 tmem_ld8(ta, r0);
@@ -376,42 +379,51 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         }
     };
 
+    // Pipeline: the MMAs of modulus k+1 (accumulator set (k+1) & 1) are issued
+    // as soon as every thread has written its data residues, and run while the
+    // epilogue of modulus k reads set k & 1.  The constant planes of modulus
+    // k+2 go into the B buffer of modulus k once its MMAs have completed.
+    // Failures (a bounded wait that gave up) are combined at each CTA barrier
+    // (__syncthreads_or), so every thread leaves the loop at the same step.
+    int last_issued = -1;    // thread 0: the last modulus whose MMAs it issued
+    int last_waited = -1;    // the last modulus whose MMAs this thread waited for
     gen(0);
     tmem_wait_st();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0 && abort_flag == 0) {
+    if (tid == 0) {
         tc_fence_after();
-        if (!issue(0)) abort_flag = 1;
+        if (issue(0)) last_issued = 0;
+        else bad = true;
     } else if (tid == 32) {
         prefetch_b(1);
     }
-    __syncthreads();
-    bool ok = abort_flag == 0;
-    uint32_t mph = 0u;  // next phase parity of the MMA barrier mbar[2]
-    for (int k = 0; k < NMOD32 && ok; k++) {
+    bool ok = true;
+    for (int k = 0; k < NMOD32; k++) {
         if (k + 1 < NMOD32) gen(k + 1);
-        const bool okm = mbar_wait(smem_u32(&mbar[2]), mph, WAIT_LIMIT32);
-        mph ^= 1u;
-        tc_fence_after();
-        if (okm)
-            epilogue(k);
-        else
-            atomicExch(&abort_flag, 1);
         tmem_wait_st();
         tc_fence_before();
-        __syncthreads();
-        if (abort_flag) {
+        if (__syncthreads_or(bad)) {  // residues of modulus k+1 written; epilogue k-1 done
             ok = false;
             break;
         }
         if (tid == 0 && k + 1 < NMOD32) {
             tc_fence_after();
-            if (!issue(k + 1)) abort_flag = 1;
-        } else if (tid == 32 && k + 2 < NMOD32) {
-            prefetch_b(k + 2);
+            if (issue(k + 1)) last_issued = k + 1;
+            else bad = true;
         }
+        const bool okm = mbar_wait(smem_u32(&mbar[2 + (k & 1)]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT32);
+        tc_fence_after();
+        if (!okm) {
+            bad = true;
+            continue;
+        }
+        last_waited = k;
+        if (tid == 32 && k + 2 < NMOD32) prefetch_b(k + 2);  // B buffer k & 1 is free again
+        epilogue(k);
     }
+    uint32_t mph = 0u;     // next phase parity of the Phase-A MMA barrier mbar[6]
+    bool pendA = false;    // thread 0: a Phase-A commit is outstanding
 
     // ---------------- CRT Phase A (FP16 tensor cores), then Phase B + pack ----------------
     if (ok) {
@@ -425,8 +437,8 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         tmem_wait_st();
         tc_fence_before();
         fence_async_smem();
-        const int bad = mbar_wait(smem_u32(&mbar[3]), 0, WAIT_LIMIT32) ? 0 : 1;
-        ok = __syncthreads_or(bad) == 0;
+        const bool okp = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT32);
+        ok = __syncthreads_or(bad || !okp) == 0;
         const uint32_t idescA = instr_desc(128, PA32_N, 0);
         const uint64_t adescA = smem_desc(smem_u32(sStage), 128, PA32_ROWB);
         const uint64_t bdescA = smem_desc(smem_u32(sPAB), 128, 256);
@@ -442,10 +454,14 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
                     tc_mma_f16(tmem + (uint32_t)(bi * PA32_N), ad, bdescA, idescA, 1);
                     ad += 16 * PA32_ROWB / 16;  // next row block: 16 row groups
                 }
-                tc_commit(smem_u32(&mbar[2]));
+                tc_commit(smem_u32(&mbar[6]));
+                pendA = true;
             }
-            const bool okA = mbar_wait(smem_u32(&mbar[2]), mph, WAIT_LIMIT32);
-            mph ^= 1u;
+            const bool okA = mbar_wait(smem_u32(&mbar[6]), mph, WAIT_LIMIT32);
+            if (okA) {
+                mph ^= 1u;
+                pendA = false;
+            }
             tc_fence_after();
             if (okA) {
                 for (int bi = qd; bi < nb; bi += 4) {
@@ -475,25 +491,25 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
                     const int kout = b0 + bi;
                     if (cvalid) out[obase + (int64_t)kout * ostride] = make_float2(re, im);
                 }
-            } else {
-                atomicExch(&abort_flag, 1);
             }
             tmem_wait_st();
             tc_fence_before();
-            __syncthreads();
-            if (abort_flag) ok = false;
+            if (__syncthreads_or(!okA)) ok = false;
         }
     }
     if (!ok && tid == 0) {
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
-        // let in-flight MMAs and copies drain (bounded) before the TMEM is freed
-        mbar_wait(smem_u32(&mbar[2]), mph, WAIT_LIMIT32);
-        if (tma_in) mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT32);
-        mbar_wait(smem_u32(&mbar[3]), 0, WAIT_LIMIT32);
+        // let this thread's in-flight MMAs and copies drain (bounded) before the
+        // TMEM is freed and the CTA exits
+        for (int j = last_waited + 1; j <= last_issued; j++)
+            mbar_wait(smem_u32(&mbar[2 + (j & 1)]), (uint32_t)((j >> 1) & 1), WAIT_LIMIT32);
+        if (pendA) mbar_wait(smem_u32(&mbar[6]), mph, WAIT_LIMIT32);
+        if (tma_in) mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT32);
+        mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT32);
     }
     tc_fence_before();
     __syncthreads();
-    if (w == 0) tmem_dealloc(tmem, 256);
+    if (w == 0) tmem_dealloc(tmem, 512);
 }
 
 cudaError_t fp32_upload_constants() {

@@ -97,6 +97,9 @@ constexpr int FP8_WARPS = 16;
 // cache, uploaded once per device when the first FP8 plan is created.
 __constant__ ModConsts c_fp8_mc;
 constexpr uint32_t APL_BASE = 320, APL_COLS = 48, N_ABUF = 2;
+// FP16 carrier: TMEM columns of one accumulator set (two classes, Re | Im, at
+// npad = 32); the second set follows the first, below the A buffers
+constexpr uint32_t F16_ACC = 128;
 
 template <int NPAD>
 struct Fp8Cfg {
@@ -392,6 +395,11 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     __shared__ __align__(8) uint64_t mbar[6];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
+    // FP16 carrier pipeline: failure flags of the steps, read by every thread
+    // right after the barrier that starts step t from slot t & 1; failures are
+    // written to the slot of the step whose barrier follows them, so no thread
+    // reads a slot that another thread may still be writing
+    __shared__ int fail[2];
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int sub = w & 3, qd = w >> 2;
@@ -429,6 +437,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const InputTile itile = input_tile(map, ncols, cbase);
         if (lane == 0) {
             abort_flag = 0;
+            if (CAR) fail[0] = fail[1] = 0;
             s_e0 = itile.e0;
             for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
             mbar_fence_init();
@@ -590,14 +599,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * CC::A_COLS;
         const int kind = fp8_kind(k);
         if constexpr (CAR)
-            issue_modulus_f16<NPAD>(tmem, apl, bd);
+            issue_modulus_f16<NPAD>(tmem + (uint32_t)(k & 1) * F16_ACC, apl, bd);
         else if (kind == KIND_SQ)
             issue_modulus_nm<KIND_SQ>(tmem, apl, bd, NPAD);
         else if (kind == KIND_B9)
             issue_modulus_nm<KIND_B9>(tmem, apl, bd, NPAD);
         else
             issue_modulus_nm<KIND_B11>(tmem, apl, bd, NPAD);
-        tc_commit(smem_u32(&mbar[2]));
+        tc_commit(smem_u32(&mbar[CAR ? 2 + (k & 1) : 2]));
         return true;
     };
 
@@ -614,46 +623,88 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     __syncthreads();
     bool ok = abort_flag == 0;
     uint32_t mph[1] = {0u};  // next phase parity of the MMA barrier mbar[2]
-    for (int k = 0; k < NSTEP && ok; k++) {
-        if (k + 1 < NMOD) gen(k + 1);  // digits of the next modulus while this one's MMAs run
-        const bool okm = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
-        mph[0] ^= 1u;
-        tc_fence_after();
-        if (okm) {
-            const uint32_t tre = tmem + lanebase + (uint32_t)(qd * OPT);
-            const int kind = fp8_kind(k);
-            if constexpr (CAR)
-                epilogue_modulus<KIND_F16, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
-            else if (kind == KIND_SQ)
-                epilogue_modulus<KIND_SQ, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
-            else if (kind == KIND_B9)
-                epilogue_modulus<KIND_B9, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
-            else
-                epilogue_modulus<KIND_B11, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
-        } else {
-            atomicExch(&abort_flag, 1);
-        }
-        tmem_wait_st();
-        tc_fence_before();
-        __syncthreads();
-        if (abort_flag) {
-            ok = false;
-            break;
-        }
-        // MMAs of modulus k+1 from thread 0; the constant planes of modulus k+2
-        // from another warp, into the buffer of modulus k (its MMAs completed:
-        // every thread waited for them before this barrier)
-        if (tid == 0 && k + 1 < NSTEP) {
+    uint32_t mph3 = 0u;      // next phase parity of mbar[3]
+    int last_issued = 0, last_waited = -1;  // FP16 carrier, thread 0: MMA batches in flight
+    if constexpr (CAR) {
+        // FP16 carrier: two accumulator sets.  The MMAs of modulus k+1 (set
+        // (k+1) & 1, committed to mbar[2 + ((k+1) & 1)]) are issued as soon as
+        // every thread has written its data residues, and run while the
+        // epilogue of modulus k reads set k & 1.  The constant planes of
+        // modulus k+2 (after the last modulus: the Phase-A constants) go into
+        // the B buffer of modulus k once its MMAs have completed.
+        for (int k = 0; k < NSTEP && ok; k++) {
+            if (k + 1 < NMOD) gen(k + 1);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncthreads();  // residues of modulus k+1 written; epilogue k-1 done
+            if (fail[k & 1]) {
+                ok = false;
+                break;
+            }
+            if (tid == 0 && k + 1 < NSTEP) {
+                tc_fence_after();
+                if (issue(k + 1)) last_issued = k + 1;
+                else atomicExch(&fail[(k + 1) & 1], 1);
+            }
+            const bool okm = mbar_wait(smem_u32(&mbar[2 + (k & 1)]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT);
             tc_fence_after();
-            if (!issue(k + 1)) abort_flag = 1;
-        } else if (tid == 32 && k + 2 < NSTEP) {
-            prefetch_b(k + 2);
-        } else if (CAR && tid == 32 && k + 2 == NSTEP) {
-            // FP16 carrier: Phase-A constants into B buffer 0 (modulus k's, done)
-            mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
-            tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
+            if (!okm) {
+                atomicExch(&fail[(k + 1) & 1], 1);
+                continue;
+            }
+            last_waited = k;
+            if (tid == 32) {
+                if (k + 2 < NSTEP) {
+                    prefetch_b(k + 2);
+                } else if (k + 2 == NSTEP) {
+                    mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
+                    tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
+                }
+            }
+            const uint32_t tre = tmem + lanebase + (uint32_t)(k & 1) * F16_ACC + (uint32_t)(qd * OPT);
+            epilogue_modulus<KIND_F16, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
         }
-        // an abort raised by issue() is seen after the next step's barrier
+        mph[0] = (uint32_t)(((NSTEP + 1) / 2) & 1);
+        mph3 = (uint32_t)((NSTEP / 2) & 1);
+    } else {
+        // A failure flag raised after a step's barrier (issue() giving up) is
+        // only written once its bounded wait has run out, long after every
+        // other thread has read the flag behind that barrier; it is seen at
+        // the next step's barrier.
+        for (int k = 0; k < NSTEP && ok; k++) {
+            if (k + 1 < NMOD) gen(k + 1);  // digits of the next modulus while this one's MMAs run
+            const bool okm = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+            mph[0] ^= 1u;
+            tc_fence_after();
+            if (okm) {
+                const uint32_t tre = tmem + lanebase + (uint32_t)(qd * OPT);
+                const int kind = fp8_kind(k);
+                if (kind == KIND_SQ)
+                    epilogue_modulus<KIND_SQ, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+                else if (kind == KIND_B9)
+                    epilogue_modulus<KIND_B9, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+                else
+                    epilogue_modulus<KIND_B11, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+            } else {
+                atomicExch(&abort_flag, 1);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncthreads();
+            if (abort_flag) {
+                ok = false;
+                break;
+            }
+            // MMAs of modulus k+1 from thread 0; the constant planes of modulus k+2
+            // from another warp, into the buffer of modulus k (its MMAs completed:
+            // every thread waited for them before this barrier)
+            if (tid == 0 && k + 1 < NSTEP) {
+                tc_fence_after();
+                if (!issue(k + 1)) abort_flag = 1;
+            } else if (tid == 32 && k + 2 < NSTEP) {
+                prefetch_b(k + 2);
+            }
+        }
     }
 
     // ---------------- CRT Phase A on FP16 tensor cores, then Kulisch + lift + pack ----
@@ -662,7 +713,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // pattern of 2^23 + P is 0x4B000000 + P); each thread presets the next
     // wave's columns right after reading them, so one CTA barrier per wave
     // orders both the reads and the presets before the next wave's MMAs.
-    uint32_t mph3 = 0u;   // next phase parity of mbar[3] (second commit group of a Phase-A wave)
     bool pend3 = false;   // a commit to mbar[3] is in flight (thread 0's view)
     if (ok) {
         const int per_wave = Kout % 8 == 0 ? 8 : 10;  // 8: two row blocks per quarter-warp per wave
@@ -678,6 +728,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         fence_async_smem();
         const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
         ok = __syncthreads_or(bad) == 0;  // uniform decision across the CTA
+        if (CAR && fail[NSTEP & 1]) ok = false;  // a failed wait in the last pipeline step
         const uint32_t idescA = instr_desc(128, PA_N, 0);
         const uint64_t adescA = smem_desc(smem_u32(sStage), 128, PA_ROWB);
         const uint64_t bdescA0 = smem_desc(smem_u32(sPAB), 128, 512), bdescA1 = smem_desc(smem_u32(sPAB) + 256, 128, 512);
@@ -768,6 +819,11 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
         // let in-flight MMAs and copies drain (bounded) before the TMEM is freed
         // and the CTA exits
+        if constexpr (CAR) {
+            // modulus MMA batches issued and not yet waited for by this thread
+            for (int j = last_waited + 1; j <= last_issued; j++)
+                mbar_wait(smem_u32(&mbar[2 + (j & 1)]), (uint32_t)((j >> 1) & 1), WAIT_LIMIT);
+        }
         mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
         if (pend3) mbar_wait(smem_u32(&mbar[3]), mph3, WAIT_LIMIT);
         mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
