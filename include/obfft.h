@@ -218,17 +218,20 @@ obfft_status obfft_host_crt_constants32(uint32_t *moduli, uint8_t *u_slices, uin
  * xt: device int64 [n_unique], |x~| < 2^53; variant 0 = the stage kernels'
  * 20/20/16-bit pieces with Barrett, 1 = dp4a over the bytes of x~ + 2^55,
  * 2 = 64-bit remainder.
- * Both: item i < n_total uses input i mod n_unique; the results of the first
+ * Both: item i < n_total uses input i mod n_unique, computed `reps` times
+ * (reps >= 1) with the input perturbed by the repetition index r (slice sum
+ * P_0 + r, or x~ + r), so that a timing launch is bound by the arithmetic
+ * rather than by loading inputs; the repetition-0 results of the first
  * n_unique items go to out (double [n_unique]) / res (uint16 [n_unique][12])
  * when those are non-NULL; *checksum (device uint64, caller-initialised) is
  * XOR-combined with a hash of every result.  Asynchronous on `stream`.
- * OBFFT_ERR_ARG for an unknown variant, n_unique < 1, n_total < 0 or NULL
- * inputs.
+ * OBFFT_ERR_ARG for an unknown variant, n_unique < 1, n_total < 0, reps < 1
+ * or NULL inputs.
  */
-obfft_status obfft_ablation_phase_b(int variant, int64_t n_unique, int64_t n_total, const void *acc,
+obfft_status obfft_ablation_phase_b(int variant, int64_t n_unique, int64_t n_total, int reps, const void *acc,
                                     const void *et, void *out, void *checksum, void *stream);
-obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_total, const void *xt, void *res,
-                                     void *checksum, void *stream);
+obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_total, int reps, const void *xt,
+                                     void *res, void *checksum, void *stream);
 
 /*
  * Largest grid (n0 * n1 * n2 complex128 values) obfft_exec_fp64_noalloc accepts.

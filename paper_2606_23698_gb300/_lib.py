@@ -87,9 +87,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_selftest_bounded_wait.restype = i32
     L.obfft_exec_fp64_noalloc.argtypes = [vp, vp, i64, i64, i64, i32, vp]
     L.obfft_exec_fp64_noalloc.restype = i32
-    L.obfft_ablation_phase_b.argtypes = [i32, i64, i64, vp, vp, vp, vp, vp]
+    L.obfft_ablation_phase_b.argtypes = [i32, i64, i64, i32, vp, vp, vp, vp, vp]
     L.obfft_ablation_phase_b.restype = i32
-    L.obfft_ablation_residues.argtypes = [i32, i64, i64, vp, vp, vp, vp]
+    L.obfft_ablation_residues.argtypes = [i32, i64, i64, i32, vp, vp, vp, vp]
     L.obfft_ablation_residues.restype = i32
     _lib = L
     return L
@@ -179,15 +179,16 @@ def obfft_host_crt_constants32():
 
 
 def obfft_ablation_phase_b(variant: int, n_unique: int, n_total: int, acc_ptr: int, et_ptr: int,
-                           out_ptr: int | None, checksum_ptr: int, stream: int = 0) -> None:
-    """Phase B of n_total scalar outputs in one accumulator layout (device pointers)."""
-    check(load().obfft_ablation_phase_b(variant, n_unique, n_total, acc_ptr, et_ptr, out_ptr, checksum_ptr, stream))
+                           out_ptr: int | None, checksum_ptr: int, stream: int = 0, reps: int = 1) -> None:
+    """Phase B of n_total x reps scalar outputs in one accumulator layout (device pointers)."""
+    check(load().obfft_ablation_phase_b(variant, n_unique, n_total, reps, acc_ptr, et_ptr, out_ptr, checksum_ptr,
+                                        stream))
 
 
 def obfft_ablation_residues(variant: int, n_unique: int, n_total: int, xt_ptr: int, res_ptr: int | None,
-                            checksum_ptr: int, stream: int = 0) -> None:
-    """Residues of n_total deconstructed integers in one instruction form (device pointers)."""
-    check(load().obfft_ablation_residues(variant, n_unique, n_total, xt_ptr, res_ptr, checksum_ptr, stream))
+                            checksum_ptr: int, stream: int = 0, reps: int = 1) -> None:
+    """Residues of n_total x reps deconstructed integers in one instruction form (device pointers)."""
+    check(load().obfft_ablation_residues(variant, n_unique, n_total, reps, xt_ptr, res_ptr, checksum_ptr, stream))
 
 
 def obfft_last_error() -> str:

@@ -60,19 +60,24 @@ def _time(fn, reps=3):
     return a.elapsed_time(b) / reps
 
 
-def measure(n_unique: int = 1 << 18, n_total: int = 1 << 27):
-    """ns per item and items per second of every variant (inputs L2-resident)."""
+def measure(n_unique: int = 1 << 18, n_total: int = 1 << 24, reps: int = 16):
+    """ns per item and items per second of every variant: n_total items from
+    n_unique L2-resident inputs, each computed `reps` times (perturbed), so the
+    launches are bound by the arithmetic."""
     acc, et = phase_b_inputs(n_unique)
     dacc = torch.from_numpy(acc.view(np.int32)).cuda()
     det = torch.from_numpy(et).cuda()
     ck = torch.zeros(1, dtype=torch.int64, device="cuda")
-    out = {"n_unique": n_unique, "n_total": n_total, "phase_b": {}, "residues": {}}
+    out = {"n_unique": n_unique, "n_total": n_total, "reps": reps, "phase_b": {}, "residues": {}}
     for v in PHASE_B_VARIANTS:
         ms = _time(lambda: _lib.obfft_ablation_phase_b(v, n_unique, n_total, dacc.data_ptr(), det.data_ptr(),
-                                                       None, ck.data_ptr()))
-        out["phase_b"][str(v)] = {"ns_per_output": ms * 1e6 / n_total, "G_outputs_per_s": n_total / ms / 1e6}
+                                                       None, ck.data_ptr(), reps=reps))
+        n = n_total * reps
+        out["phase_b"][str(v)] = {"ns_per_output": ms * 1e6 / n, "G_outputs_per_s": n / ms / 1e6}
     xt = torch.from_numpy(residue_inputs(n_unique)).cuda()
     for v in RESIDUE_VARIANTS:
-        ms = _time(lambda: _lib.obfft_ablation_residues(v, n_unique, n_total, xt.data_ptr(), None, ck.data_ptr()))
-        out["residues"][str(v)] = {"ns_per_element": ms * 1e6 / n_total, "G_elements_per_s": n_total / ms / 1e6}
+        ms = _time(lambda: _lib.obfft_ablation_residues(v, n_unique, n_total, xt.data_ptr(), None, ck.data_ptr(),
+                                                        reps=reps))
+        n = n_total * reps
+        out["residues"][str(v)] = {"ns_per_element": ms * 1e6 / n, "G_elements_per_s": n / ms / 1e6}
     return out

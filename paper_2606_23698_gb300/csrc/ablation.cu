@@ -26,10 +26,11 @@
 //   variant 2: the compiler's 64-bit remainder (reference form).
 //
 // Each kernel reads n_unique inputs (small enough to stay in L2) and processes
-// n_total items, item i using input i mod n_unique; results of the first
-// n_unique items are stored when `out` is given, and every result is folded
-// into a 64-bit XOR checksum, so a timing launch with n_total >> n_unique is
-// bound by the arithmetic, not by memory.
+// n_total items, item i using input i mod n_unique, `reps` times each with the
+// input perturbed by the repetition index (slice sum P_0 + r, or x~ + r), so
+// that a timing launch does reps times the arithmetic per byte loaded.  The
+// results of the first n_unique items (repetition 0) are stored when `out` is
+// given; every result is folded into a 64-bit XOR checksum.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -104,7 +105,7 @@ __device__ __forceinline__ void kw_resolve(const KulischWords<RHO, LANES> &acc, 
 template <int VARIANT>
 __global__ void __launch_bounds__(ABL_THREADS) phase_b_ablation_kernel(const uint32_t *__restrict__ acc,
                                                                        const int *__restrict__ et,
-                                                                       int64_t n_unique, int64_t n_total,
+                                                                       int64_t n_unique, int64_t n_total, int reps,
                                                                        double *__restrict__ out,
                                                                        unsigned long long *checksum) {
     const ModConsts &mc = c_abl_mc;
@@ -118,6 +119,9 @@ __global__ void __launch_bounds__(ABL_THREADS) phase_b_ablation_kernel(const uin
 #pragma unroll
         for (int j = 0; j < 21; j++) wv[j] = acc[u * 21 + j];
         const int e = et[u];
+        const uint32_t w00 = wv[0];
+        for (int r = 0; r < reps; r++) {
+        wv[0] = w00 + (uint32_t)r;
         double y;
         bool slow, near;
         uint32_t Rw[4];
@@ -137,15 +141,16 @@ __global__ void __launch_bounds__(ABL_THREADS) phase_b_ablation_kernel(const uin
             y = lift_pack_fast(ew[0], ew[1], ew[2], ew[3], wv + S_RAW, mc, e, off, zbias, slow, Rw, near);
         }
         if (slow) y = kulisch_finish_general(Rw[0], Rw[1], Rw[2], Rw[3], near, e, mc);
-        if (out && i < n_unique) out[i] = y;
-        x ^= (uint64_t)__double_as_longlong(y) + (uint64_t)i;
+        if (out && i < n_unique && r == 0) out[i] = y;
+        x ^= (uint64_t)__double_as_longlong(y) + (uint64_t)(i + r);
+        }
     }
     atomicXor(checksum, (unsigned long long)x);
 }
 
 template <int VARIANT>
 __global__ void __launch_bounds__(ABL_THREADS) residue_ablation_kernel(const int64_t *__restrict__ xt,
-                                                                       int64_t n_unique, int64_t n_total,
+                                                                       int64_t n_unique, int64_t n_total, int reps,
                                                                        uint16_t *__restrict__ res,
                                                                        unsigned long long *checksum) {
     const ModConsts &mc = c_abl_mc;
@@ -153,7 +158,9 @@ __global__ void __launch_bounds__(ABL_THREADS) residue_ablation_kernel(const int
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = i % n_unique;
-        const uint64_t v = (uint64_t)(xt[u] + (1ll << 55));  // in [2^54, 2^56)
+        const int64_t x0 = xt[u];
+        for (int rp = 0; rp < reps; rp++) {
+        const uint64_t v = (uint64_t)(x0 + rp + (1ll << 55));  // in [2^54, 2^56)
         uint32_t r[NMOD];
 #pragma unroll
         for (int k = 0; k < NMOD; k++) {
@@ -179,14 +186,15 @@ __global__ void __launch_bounds__(ABL_THREADS) residue_ablation_kernel(const int
             t = t >= m ? t - m : t;
             r[k] = t;
         }
-        if (res && i < n_unique) {
+        if (res && i < n_unique && rp == 0) {
 #pragma unroll
             for (int k = 0; k < NMOD; k++) res[i * NMOD + k] = (uint16_t)r[k];
         }
-        uint64_t h = (uint64_t)i;
+        uint64_t h = (uint64_t)(i + rp);
 #pragma unroll
         for (int k = 0; k < NMOD; k++) h = h * 0x9E3779B97F4A7C15ull + r[k];
         x ^= h;
+        }
     }
     atomicXor(checksum, (unsigned long long)x);
 }
@@ -205,30 +213,30 @@ static unsigned abl_blocks(int64_t n_total) {
     return (unsigned)(want < cap ? want : cap);
 }
 
-cudaError_t launch_phase_b_ablation(int variant, int64_t n_unique, int64_t n_total, const uint32_t *acc,
+cudaError_t launch_phase_b_ablation(int variant, int64_t n_unique, int64_t n_total, int reps, const uint32_t *acc,
                                     const int *et, double *out, unsigned long long *checksum, cudaStream_t s) {
     cudaError_t e = abl_upload();
     if (e != cudaSuccess) return e;
     const unsigned nb = abl_blocks(n_total);
     switch (variant) {
-        case 0: phase_b_ablation_kernel<0><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, out, checksum); break;
-        case 32: phase_b_ablation_kernel<32><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, out, checksum); break;
-        case 16: phase_b_ablation_kernel<16><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, out, checksum); break;
-        case 8: phase_b_ablation_kernel<8><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, out, checksum); break;
+        case 0: phase_b_ablation_kernel<0><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, reps, out, checksum); break;
+        case 32: phase_b_ablation_kernel<32><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, reps, out, checksum); break;
+        case 16: phase_b_ablation_kernel<16><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, reps, out, checksum); break;
+        case 8: phase_b_ablation_kernel<8><<<nb, ABL_THREADS, 0, s>>>(acc, et, n_unique, n_total, reps, out, checksum); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_residue_ablation(int variant, int64_t n_unique, int64_t n_total, const int64_t *xt,
+cudaError_t launch_residue_ablation(int variant, int64_t n_unique, int64_t n_total, int reps, const int64_t *xt,
                                     uint16_t *res, unsigned long long *checksum, cudaStream_t s) {
     cudaError_t e = abl_upload();
     if (e != cudaSuccess) return e;
     const unsigned nb = abl_blocks(n_total);
     switch (variant) {
-        case 0: residue_ablation_kernel<0><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, res, checksum); break;
-        case 1: residue_ablation_kernel<1><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, res, checksum); break;
-        case 2: residue_ablation_kernel<2><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, res, checksum); break;
+        case 0: residue_ablation_kernel<0><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, reps, res, checksum); break;
+        case 1: residue_ablation_kernel<1><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, reps, res, checksum); break;
+        case 2: residue_ablation_kernel<2><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, reps, res, checksum); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

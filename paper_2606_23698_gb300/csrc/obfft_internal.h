@@ -166,9 +166,9 @@ cudaError_t launch_bounded_wait_selftest(int *status, cudaStream_t s);
 std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K);
 std::vector<uint8_t> build_phase_a_b();
 // Epilogue ablation kernels (ablation.cu)
-cudaError_t launch_phase_b_ablation(int variant, int64_t n_unique, int64_t n_total, const uint32_t *acc,
+cudaError_t launch_phase_b_ablation(int variant, int64_t n_unique, int64_t n_total, int reps, const uint32_t *acc,
                                     const int *et, double *out, unsigned long long *checksum, cudaStream_t s);
-cudaError_t launch_residue_ablation(int variant, int64_t n_unique, int64_t n_total, const int64_t *xt,
+cudaError_t launch_residue_ablation(int variant, int64_t n_unique, int64_t n_total, int reps, const int64_t *xt,
                                     uint16_t *res, unsigned long long *checksum, cudaStream_t s);
 cudaError_t launch_stage_fp64(const AxisTables &t, const StageGeom &g, int stage,
                               const double2 *in, double2 *out, cudaStream_t s);

@@ -1180,21 +1180,23 @@ extern "C" obfft_status obfft_host_crt_constants32(uint32_t *moduli, uint8_t *u_
     return OBFFT_OK;
 }
 
-extern "C" obfft_status obfft_ablation_phase_b(int variant, int64_t n_unique, int64_t n_total, const void *acc,
-                                              const void *et, void *out, void *checksum, void *stream) {
+extern "C" obfft_status obfft_ablation_phase_b(int variant, int64_t n_unique, int64_t n_total, int reps,
+                                              const void *acc, const void *et, void *out, void *checksum,
+                                              void *stream) {
     if (variant != 0 && variant != 32 && variant != 16 && variant != 8)
         return set_error(OBFFT_ERR_ARG, "variant must be 0, 32, 16 or 8");
-    if (n_unique < 1 || n_total < 0 || !acc || !et || !checksum) return set_error(OBFFT_ERR_ARG, "bad argument");
-    cudaError_t e = launch_phase_b_ablation(variant, n_unique, n_total, (const uint32_t *)acc, (const int *)et,
+    if (n_unique < 1 || n_total < 0 || reps < 1 || !acc || !et || !checksum)
+        return set_error(OBFFT_ERR_ARG, "bad argument");
+    cudaError_t e = launch_phase_b_ablation(variant, n_unique, n_total, reps, (const uint32_t *)acc, (const int *)et,
                                             (double *)out, (unsigned long long *)checksum, (cudaStream_t)stream);
     return e == cudaSuccess ? OBFFT_OK : set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
 }
 
-extern "C" obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_total, const void *xt,
-                                               void *res, void *checksum, void *stream) {
+extern "C" obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_total, int reps,
+                                               const void *xt, void *res, void *checksum, void *stream) {
     if (variant < 0 || variant > 2) return set_error(OBFFT_ERR_ARG, "variant must be 0, 1 or 2");
-    if (n_unique < 1 || n_total < 0 || !xt || !checksum) return set_error(OBFFT_ERR_ARG, "bad argument");
-    cudaError_t e = launch_residue_ablation(variant, n_unique, n_total, (const int64_t *)xt, (uint16_t *)res,
+    if (n_unique < 1 || n_total < 0 || reps < 1 || !xt || !checksum) return set_error(OBFFT_ERR_ARG, "bad argument");
+    cudaError_t e = launch_residue_ablation(variant, n_unique, n_total, reps, (const int64_t *)xt, (uint16_t *)res,
                                             (unsigned long long *)checksum, (cudaStream_t)stream);
     return e == cudaSuccess ? OBFFT_OK : set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
 }

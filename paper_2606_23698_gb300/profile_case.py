@@ -7,7 +7,8 @@
 `stage` runs a single stage launch (Bailey stage 1 or 2 of one axis pass) of a
 D0 x D1 x D2 plan on seeded uniform input; `fft3` runs one forward transform;
 `ablation` runs each epilogue ablation kernel once (4 Phase-B word layouts,
-3 residue forms; 2^22 items from 2^16 L2-resident inputs).
+3 residue forms; 2^22 items from 2^16 L2-resident inputs, 16 perturbed
+repetitions each).
 Both print one line and exit 0, so the same command can run once plainly and
 then under a profiler restricted to the kernel of interest.
 """
@@ -44,10 +45,10 @@ def main(argv):
         dacc, det = torch.from_numpy(acc.view(np.int32)).cuda(), torch.from_numpy(et).cuda()
         ck = torch.zeros(1, dtype=torch.int64, device="cuda")
         for v in PHASE_B_VARIANTS:
-            _lib.obfft_ablation_phase_b(v, nu, nt, dacc.data_ptr(), det.data_ptr(), None, ck.data_ptr())
+            _lib.obfft_ablation_phase_b(v, nu, nt, dacc.data_ptr(), det.data_ptr(), None, ck.data_ptr(), reps=16)
         xt = torch.from_numpy(residue_inputs(nu)).cuda()
         for v in RESIDUE_VARIANTS:
-            _lib.obfft_ablation_residues(v, nu, nt, xt.data_ptr(), None, ck.data_ptr())
+            _lib.obfft_ablation_residues(v, nu, nt, xt.data_ptr(), None, ck.data_ptr(), reps=16)
         torch.cuda.synchronize()
         print("ok ablation", int(ck.item()))
         return

@@ -70,7 +70,7 @@ def test_phase_b_all_word_widths_exact():
         assert bad.size == 0, (variant, [(vals[i], ets[i], got[i], want[i]) for i in bad[:3]])
         # a longer launch over the same inputs (item i uses input i mod n)
         ck2 = torch.zeros(1, dtype=torch.int64, device="cuda")
-        _lib.obfft_ablation_phase_b(variant, n, 7 * n, dacc.data_ptr(), det.data_ptr(), None, ck2.data_ptr())
+        _lib.obfft_ablation_phase_b(variant, n, 7 * n, dacc.data_ptr(), det.data_ptr(), None, ck2.data_ptr(), reps=3)
         torch.cuda.synchronize()
         sums[variant] = (int(ck.item()), int(ck2.item()))
     assert len(set(sums.values())) == 1
