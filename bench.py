@@ -24,6 +24,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "1024^3 Z2Z 3-D FFT ms & % roofline: Ozaki FP8/INT8 vs native FP64, err≤1e-14"
+# mma.sync m16n8k32 s8 rate measured on this GPU by probes/simt_int8_peak.cu
+INT8_MMA_SYNC_TOPS = 150.9
 SHAPE = (1024, 1024, 1024)
 
 
@@ -485,6 +487,12 @@ def main():
                        "mode": mode, "seed": 20260003, "l2": "inputs larger than L2",
                        "parallelism": "replicas" if world > 1 else "single"},
             "gflops_5nlogn": gflops, "modes_ms": modes, "rel_diff_vs_fp64_native": diff,
+            # INT8 mode: 1.125 mma.sync m16n8k32 s8 (8192 ops each) per complex output
+            # and stage, 6 stages per transform, against the measured mma.sync peak
+            "int8_tensor": ({"tops": 6 * N3 * 1.125 * 8192 / (modes["int8"] * 1e-3) / 1e12,
+                             "peak_tops": INT8_MMA_SYNC_TOPS,
+                             "frac": 6 * N3 * 1.125 * 8192 / (modes["int8"] * 1e-3) / 1e12 / INT8_MMA_SYNC_TOPS}
+                            if "int8" in modes else None),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "side_configs": extra, "fp32_variant": fp32,
             "epilogue_ablation": ablation}
