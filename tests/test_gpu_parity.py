@@ -105,7 +105,7 @@ def test_wide_range_256_stage_sampled(mode):
     _check_pass_sampled(pl, x, shape, dir=-1, nsample=48)
 
 
-@pytest.mark.parametrize("mode", ["fp8", "fp16"])
+@pytest.mark.parametrize("mode", ["fp8", "fp16", "int8"])
 def test_full_size_1024cube_sampled_and_parseval(mode):
     """The benchmark workload itself (1024^3, splits 32 x 32, uniform[-1,1)):
     every stage of every axis pass matches the oracle bit for bit on sampled
