@@ -567,13 +567,17 @@ void ob_ref_dft_dd_axis(int64_t nlines, int N, const double *in, const double *t
 }
 
 /* One output Y[k0,k1,k2] of the 3-D DFT of a double grid x [n0][n1][n2][2],
- * in double-double, summed separably (innermost axis first). tw_a: [n_a][4]. */
+ * in double-double, summed separably (innermost axis first). tw_a: [n_a][4].
+ * The j0 slices are summed in parallel into per-slice partial results, which
+ * are then combined in j0 order: the result does not depend on the thread
+ * count. */
 void ob_ref_dft_dd_point(int n0, int n1, int n2, const double *x,
                          const double *tw0, const double *tw1, const double *tw2,
                          int k0, int k1, int k2, double *res /* [4] */) {
-    dd Ur = {0, 0}, Ui = {0, 0};
+    dd *Tr = (dd *)malloc(sizeof(dd) * (size_t)n0), *Ti = (dd *)malloc(sizeof(dd) * (size_t)n0);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int j0 = 0; j0 < n0; j0++) {
-        dd Tr = {0, 0}, Ti = {0, 0};
+        dd tr = {0, 0}, ti = {0, 0};
         for (int j1 = 0; j1 < n1; j1++) {
             dd Sr = {0, 0}, Si = {0, 0};
             const double *xr = x + (((int64_t)j0 * n1 + j1) * n2) * 2;
@@ -586,13 +590,20 @@ void ob_ref_dft_dd_point(int n0, int n1, int n2, const double *x,
             }
             int m = (int)(((int64_t)j1 * k1) % n1);
             dd wr = {tw1[4 * m], tw1[4 * m + 1]}, wi = {tw1[4 * m + 2], tw1[4 * m + 3]};
-            Tr = dd_add(Tr, dd_add(dd_mul(wr, Sr), dd_neg(dd_mul(wi, Si))));
-            Ti = dd_add(Ti, dd_add(dd_mul(wr, Si), dd_mul(wi, Sr)));
+            tr = dd_add(tr, dd_add(dd_mul(wr, Sr), dd_neg(dd_mul(wi, Si))));
+            ti = dd_add(ti, dd_add(dd_mul(wr, Si), dd_mul(wi, Sr)));
         }
+        Tr[j0] = tr;
+        Ti[j0] = ti;
+    }
+    dd Ur = {0, 0}, Ui = {0, 0};
+    for (int j0 = 0; j0 < n0; j0++) {
         int m = (int)(((int64_t)j0 * k0) % n0);
         dd wr = {tw0[4 * m], tw0[4 * m + 1]}, wi = {tw0[4 * m + 2], tw0[4 * m + 3]};
-        Ur = dd_add(Ur, dd_add(dd_mul(wr, Tr), dd_neg(dd_mul(wi, Ti))));
-        Ui = dd_add(Ui, dd_add(dd_mul(wr, Ti), dd_mul(wi, Tr)));
+        Ur = dd_add(Ur, dd_add(dd_mul(wr, Tr[j0]), dd_neg(dd_mul(wi, Ti[j0]))));
+        Ui = dd_add(Ui, dd_add(dd_mul(wr, Ti[j0]), dd_mul(wi, Tr[j0])));
     }
+    free(Tr);
+    free(Ti);
     res[0] = Ur.hi; res[1] = Ur.lo; res[2] = Ui.hi; res[3] = Ui.lo;
 }
