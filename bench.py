@@ -137,6 +137,20 @@ def cpu_oracle_ms_per_transform(n: int, budget_s: float = 12.0):
                       f"scaled to 3 x {n}^2 lines"
 
 
+def cpu_fp64_fft_ms_per_transform(n: int, lines: int = 1 << 15):
+    """Time the oracle's plain FP64 mixed-radix FFT (as it stands) on `lines`
+    lines of length n and scale to a full n^3 transform (3 axes x n^2 lines)."""
+    from oracle import ref
+    from synth import inputs as S
+    x = S.complex_uniform(S.SEED_1024, (lines, n)).numpy()
+    ref.fft_lines(x[:8])  # builds the library and the twiddles
+    t0 = time.perf_counter()
+    ref.fft_lines(x)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dt / lines * 3 * n * n * 1e3, cores, f"{lines} lines of {n}, scaled to 3 x {n}^2 lines"
+
+
 # -------------------------------------------------------------- reference ---
 def run_reference(args, rank, world):
     if rank != 0:
@@ -476,7 +490,9 @@ def main():
     cpu = None
     if not args.no_cpu and world == 1:
         cms, cores, sample = cpu_oracle_ms_per_transform(n, budget_s=12.0)
-        cpu = {"value": cms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+        fms, fcores, fsample = cpu_fp64_fft_ms_per_transform(n)
+        cpu = {"value": cms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
+               "fp64_fft_oracle": {"value": fms, "unit": "ms", "cores": fcores, "sample": fsample}}
     launches = 6 * args.steps  # six stage kernels per 3-D transform
     line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,

@@ -26,6 +26,8 @@
  *   ob_ref_dft_dd_axis   direct O(N^2) DFT along the last axis in
  *                  double-double arithmetic (the high-precision reference).
  *   ob_ref_dft_dd_point  one output of the 3-D DFT in double-double.
+ *   ob_ref_fft_lines     plain FP64 mixed-radix FFT along the last axis (the
+ *                  FP64 reference transform and the timed CPU FFT).
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (contraction must be
  * off: the double-double kernels rely on separately rounded products/sums).
@@ -507,6 +509,75 @@ void ob_ref_kulisch(int64_t n, const int64_t *P, const int64_t *Q, const ob_cons
         i128 Rv = kulisch_lift(P + i * S_RAW, Q + i * S_FRAC, c, zhat ? zhat + i : NULL);
         Rlimbs[2 * i] = (int64_t)(uint64_t)Rv;
         Rlimbs[2 * i + 1] = (int64_t)(uint64_t)((u128)Rv >> 64);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plain FP64 mixed-radix FFT along the last axis (the FP64 reference of the  */
+/* transform): recursive decimation in time over the smallest prime factor  */
+/* of the current length, a direct DFT for prime lengths.  tw: [N][2] =     */
+/* exp(sign 2 pi i m / N) rounded to double; every sub-length's twiddle is  */
+/* an entry of it (m scaled by N / length).  in/out: [nlines][N][2].        */
+/* ------------------------------------------------------------------------ */
+static int smallest_factor(int n) {
+    for (int f = 2; f * f <= n; f++)
+        if (n % f == 0) return f;
+    return n;
+}
+
+/* y[k] = sum_j x[j stride] w^(j k), length n, w = tw[(N / n) m] */
+static void fft_rec(int n, const double *x, int stride, double *y, const double *tw, int N, double *scratch) {
+    if (n == 1) {
+        y[0] = x[0];
+        y[1] = x[1];
+        return;
+    }
+    const int p = smallest_factor(n), m = n / p, step = N / n;
+    if (p == n) { /* prime length: direct sum */
+        for (int k = 0; k < n; k++) {
+            double sr = 0.0, si = 0.0;
+            for (int j = 0; j < n; j++) {
+                const int e = (int)(((int64_t)j * k) % n) * step;
+                const double wr = tw[2 * e], wi = tw[2 * e + 1];
+                const double ar = x[2 * j * stride], ai = x[2 * j * stride + 1];
+                sr += wr * ar - wi * ai;
+                si += wr * ai + wi * ar;
+            }
+            y[2 * k] = sr;
+            y[2 * k + 1] = si;
+        }
+        return;
+    }
+    /* p interleaved sub-transforms of length m: sub r holds x[(j p + r) stride] */
+    double *sub = scratch;            /* [p][m][2] */
+    double *rest = scratch + 2 * n;   /* scratch for the recursion */
+    for (int r = 0; r < p; r++) fft_rec(m, x + 2 * r * stride, stride * p, sub + 2 * r * m, tw, N, rest);
+    /* y[k1 + m k2] = sum_r w_n^(r k1) w_p^(r k2) sub_r[k1] */
+    for (int k1 = 0; k1 < m; k1++)
+        for (int k2 = 0; k2 < p; k2++) {
+            const int k = k1 + m * k2;
+            double sr = 0.0, si = 0.0;
+            for (int r = 0; r < p; r++) {
+                const int e = (int)(((int64_t)r * k) % n) * step;
+                const double wr = tw[2 * e], wi = tw[2 * e + 1];
+                const double ar = sub[2 * (r * m + k1)], ai = sub[2 * (r * m + k1) + 1];
+                sr += wr * ar - wi * ai;
+                si += wr * ai + wi * ar;
+            }
+            y[2 * k] = sr;
+            y[2 * k + 1] = si;
+        }
+}
+
+void ob_ref_fft_lines(int64_t nlines, int N, const double *tw, const double *in, double *out) {
+#pragma omp parallel
+    {
+        /* scratch: 2n doubles per recursion level, at most log2 N + 1 levels */
+        double *scratch = (double *)malloc(sizeof(double) * 2 * (size_t)N * 40);
+#pragma omp for schedule(static)
+        for (int64_t l = 0; l < nlines; l++)
+            fft_rec(N, in + l * (int64_t)N * 2, 1, out + l * (int64_t)N * 2, tw, N, scratch);
+        free(scratch);
     }
 }
 

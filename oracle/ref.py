@@ -85,6 +85,9 @@ def lib():
     L.ob_ref_dft_dd_axis.restype = None
     L.ob_ref_dft_dd_axis.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]
+    L.ob_ref_fft_lines.restype = None
+    L.ob_ref_fft_lines.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]
     L.ob_ref_dft_dd_point.restype = None
     L.ob_ref_dft_dd_point.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 4 + \
         [ctypes.c_int] * 3 + [ctypes.c_void_p]
@@ -325,6 +328,32 @@ def dft3d_dd_point(x: np.ndarray, k, sign: int = -1) -> np.ndarray:
                               _ptr(dd_twiddles(n2, sign)), int(k[0]), int(k[1]), int(k[2]),
                               _ptr(res))
     return res
+
+
+@lru_cache(maxsize=None)
+def fp64_twiddles(N: int, sign: int) -> np.ndarray:
+    """exp(sign 2 pi i m / N), m < N, rounded to double (from the fixed-point values)."""
+    t = dd_twiddles(N, sign)
+    return np.ascontiguousarray(np.stack([t[:, 0], t[:, 2]], axis=1))
+
+
+def fft_lines(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    """Plain FP64 mixed-radix FFT of every row of x (complex128 [L][N])."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    L, N = x.shape
+    y = np.empty_like(x)
+    lib().ob_ref_fft_lines(L, N, _ptr(fp64_twiddles(N, sign)), _ptr(x.view(np.float64)), _ptr(y.view(np.float64)))
+    return y
+
+
+def fft3d(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    """Plain FP64 3-D FFT of x [..., n0, n1, n2] (axis 2 first, then 1, then 0)."""
+    y = np.asarray(x, dtype=np.complex128)
+    for ax in (y.ndim - 1, y.ndim - 2, y.ndim - 3):
+        moved = np.moveaxis(y, ax, -1)
+        shp = moved.shape
+        y = np.moveaxis(fft_lines(np.ascontiguousarray(moved).reshape(-1, shp[-1]), sign).reshape(shp), -1, ax)
+    return np.ascontiguousarray(y)
 
 
 def dd_to_complex(y: np.ndarray) -> np.ndarray:
