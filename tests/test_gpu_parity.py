@@ -127,11 +127,14 @@ def test_full_size_1024cube_sampled_and_parseval(mode):
     torch.cuda.empty_cache()
 
 
-SPOTS_1024 = [(0, 0, 0), (1, 2, 3), (511, 17, 1000), (1023, 1023, 1023), (512, 512, 512), (5, 700, 300)]
+# 16 sampled outputs: DC, the Nyquist corner, axis-aligned and seeded random frequencies
+SPOTS_1024 = [(0, 0, 0), (1, 2, 3), (511, 17, 1000), (1023, 1023, 1023), (512, 512, 512), (5, 700, 300),
+              (0, 0, 1), (0, 1023, 0), (1, 0, 0)] + \
+    [tuple(int(v) for v in row) for row in np.random.default_rng(20260003).integers(0, 1024, (7, 3))]
 
 
 def test_full_size_1024cube_dd_spot_outputs():
-    """The benchmark workload against double-double at sampled outputs (the
+    """The benchmark workload against double-double at 16 sampled outputs (the
     oracle's separable 3-D DFT in double-double, one output at a time): the FP8
     result's normwise error over the samples is below 1e-14 and at most twice
     the native FP64 kernel's (measured: 2.8e-16 and 3.5e-16)."""
