@@ -107,7 +107,11 @@ obfft_status obfft_plan_get_splits(obfft_plan p, int grid, int axis, int *p_out,
 /*
  * Plan for `count` independent grids of possibly different sizes
  * (dims[g][0..2]) executed together (the uneven batch).  Same size rules as
- * obfft_plan_create; the scratch is sized for the largest grid.
+ * obfft_plan_create (with OBFFT_AUTOTUNE=1 in the environment the splits of
+ * each distinct axis length are chosen by timing).  Grids of identical shape
+ * and splits form a group that runs as one batched transform; the plan owns
+ * device memory of about the total size of the grids, three times that for
+ * grids that share their shape.
  */
 obfft_status obfft_plan_create_many(obfft_plan *out, int count, const int64_t *dims /* [count][3] */,
                                     int mode);
@@ -115,6 +119,9 @@ obfft_status obfft_plan_create_many(obfft_plan *out, int count, const int64_t *d
 /*
  * Transform every grid of a _many plan: ins[g] / outs[g] are device pointers
  * (arrays of `count` pointers in HOST memory).  Asynchronous on `stream`.
+ * The work (per group: device-to-device gathers of the members, six batched
+ * stage launches, scatters of the results) is captured once into a CUDA
+ * graph per set of pointers and direction, and replayed by later calls.
  */
 obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, void *const *outs, int dir,
                              void *stream);

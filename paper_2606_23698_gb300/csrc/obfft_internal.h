@@ -124,7 +124,12 @@ struct obfft_plan_s {
     std::vector<const void *> graph_ins;
     std::vector<void *> graph_outs;
     int graph_dir = 0;
-    std::vector<void *> grid_scratch;  // scratch of grid g (offsets into `scratch`)
+    // multi-grid plans: grids of identical shape and splits run together as
+    // one batched transform.  Group j lists its grid indices; a group of one
+    // grid has only a scratch slice, a larger group also a gather buffer and a
+    // result buffer (all offsets into `scratch`).
+    std::vector<std::vector<int>> groups;
+    std::vector<void *> group_in, group_out, group_scratch;
     // host-to-host execution: two grid-sized device buffers, a copy stream and
     // its events, created on the first obfft_exec_host call
     void *host_io[2] = {nullptr, nullptr};

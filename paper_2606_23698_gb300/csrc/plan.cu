@@ -726,8 +726,31 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
         maxel = std::max(maxel, (size_t)(gd.n[0] * gd.n[1] * gd.n[2]));
         sumel += (size_t)(gd.n[0] * gd.n[1] * gd.n[2]);
     }
-    // single grid: one grid-sized scratch; several grids: one slice per grid so
-    // that their launch chains do not share memory
+    // several grids: those of identical shape and splits form a group that runs
+    // as one batched transform (its stage launches cover all members); every
+    // group gets its own memory so that the groups' launch chains are independent
+    if (P->grids.size() > 1) {
+        for (int g = 0; g < (int)P->grids.size(); g++) {
+            const GridDesc &a = P->grids[g];
+            int j = 0;
+            for (; j < (int)P->groups.size(); j++) {
+                const GridDesc &b = P->grids[P->groups[j][0]];
+                bool same = true;
+                for (int x = 0; x < 3; x++)
+                    same = same && a.n[x] == b.n[x] && a.ax[x].p == b.ax[x].p && a.ax[x].q == b.ax[x].q;
+                if (same) break;
+            }
+            if (j == (int)P->groups.size()) P->groups.push_back({});
+            P->groups[j].push_back(g);
+        }
+        sumel = 0;
+        for (auto &grp : P->groups) {
+            const GridDesc &gd = P->grids[grp[0]];
+            const size_t gel = (size_t)(gd.n[0] * gd.n[1] * gd.n[2]) * grp.size();
+            sumel += grp.size() > 1 ? 3 * gel : gel;
+        }
+    }
+    // single grid: one grid-sized scratch
     const size_t eb = elem_bytes(P->mode);
     P->scratch_bytes = (P->grids.size() == 1 ? maxel * (size_t)P->batch : sumel) * eb;
     cudaError_t e = cudaMalloc(&P->scratch, P->scratch_bytes ? P->scratch_bytes : 16);
@@ -738,10 +761,21 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
         return set_error(OBFFT_ERR_ALLOC, std::string("scratch: ") + cudaGetErrorString(e));
     }
     if (P->grids.size() > 1) {
-        size_t off = 0;
-        for (auto &gd : P->grids) {
-            P->grid_scratch.push_back((char *)P->scratch + off * eb);
-            off += (size_t)(gd.n[0] * gd.n[1] * gd.n[2]);
+        char *base = (char *)P->scratch;
+        for (auto &grp : P->groups) {
+            const GridDesc &gd = P->grids[grp[0]];
+            const size_t gbytes = (size_t)(gd.n[0] * gd.n[1] * gd.n[2]) * grp.size() * eb;
+            P->group_scratch.push_back(base);
+            base += gbytes;
+            if (grp.size() > 1) {
+                P->group_in.push_back(base);
+                base += gbytes;
+                P->group_out.push_back(base);
+                base += gbytes;
+            } else {
+                P->group_in.push_back(nullptr);
+                P->group_out.push_back(nullptr);
+            }
         }
     }
     *out = P;
@@ -1086,8 +1120,26 @@ extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, vo
         e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
         obfft_status st = OBFFT_OK;
-        for (size_t g = 0; g < G && st == OBFFT_OK; g++)
-            st = exec_grid(p, p->grids[g], 1, ins[g], outs[g], dir, p->capture_stream, p->grid_scratch[g]);
+        const size_t eb = elem_bytes(p->mode);
+        for (size_t j = 0; j < p->groups.size() && st == OBFFT_OK; j++) {
+            const std::vector<int> &grp = p->groups[j];
+            const GridDesc &gd = p->grids[grp[0]];
+            if (grp.size() == 1) {
+                st = exec_grid(p, gd, 1, ins[grp[0]], outs[grp[0]], dir, p->capture_stream, p->group_scratch[j]);
+                continue;
+            }
+            // gather the members into one batch, transform, scatter the results
+            const size_t bytes = (size_t)(gd.n[0] * gd.n[1] * gd.n[2]) * eb;
+            for (size_t i = 0; i < grp.size() && st == OBFFT_OK; i++)
+                st = cuda_err(cudaMemcpyAsync((char *)p->group_in[j] + i * bytes, ins[grp[i]], bytes,
+                                              cudaMemcpyDeviceToDevice, p->capture_stream), "gather");
+            if (st == OBFFT_OK)
+                st = exec_grid(p, gd, (int64_t)grp.size(), p->group_in[j], p->group_out[j], dir, p->capture_stream,
+                               p->group_scratch[j]);
+            for (size_t i = 0; i < grp.size() && st == OBFFT_OK; i++)
+                st = cuda_err(cudaMemcpyAsync(outs[grp[i]], (char *)p->group_out[j] + i * bytes, bytes,
+                                              cudaMemcpyDeviceToDevice, p->capture_stream), "scatter");
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(p->capture_stream, &graph);
         if (st != OBFFT_OK) {
