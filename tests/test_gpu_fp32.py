@@ -240,3 +240,42 @@ def test_fp32_autograd_adjoint():
         grads[mode] = xr.grad.to(torch.complex128)
     rel = torch.linalg.vector_norm(grads["fp32"] - grads["fp64"]) / torch.linalg.vector_norm(grads["fp64"])
     assert float(rel) < 1e-6
+
+
+def test_fp32_argument_errors_and_dtype_checks():
+    """complex64 plans reject complex128 tensors and the usual bad pointers;
+    FP32-precision plans refuse factors above 32."""
+    from paper_2606_23698_gb300 import ObfftError, _lib
+    pl = plan((8, 8, 8))
+    x64 = torch.zeros(512, dtype=torch.complex64, device="cuda")
+    x128 = torch.zeros(512, dtype=torch.complex128, device="cuda")
+    with pytest.raises(TypeError):
+        pl.exec(x128)
+    with pytest.raises(ObfftError):
+        _lib.obfft_exec(pl.handle, x64.data_ptr(), x64.data_ptr(), -1, 0)      # in == out
+    with pytest.raises(ObfftError):
+        _lib.obfft_exec(pl.handle, x64.data_ptr() + 8, x64.data_ptr() + 4096, -1, 0)  # misaligned
+    with pytest.raises(ObfftError):
+        plan((8, 8, 2048))                       # 2048 = 32 x 64: a factor above 32
+    y = plan((8, 8, 4096), "fp32native")         # 64 x 64: the native comparator allows it
+    y.close()
+
+
+def test_fp32_stage_entry_matches_oracle_stage():
+    """obfft_exec_stage in the FP32 mode: one stage-1 launch against the
+    oracle's FP32 stage on every column."""
+    shape = (4, 8, 96)
+    pl = plan(shape)
+    p, q = pl.splits(2)
+    x = torch.from_numpy(c64(S.complex_uniform(3, shape).numpy())).cuda()
+    out = torch.empty_like(x)
+    pl.exec_stage(2, 1, x, out, -1)
+    torch.cuda.synchronize()
+    L, N = x.numel() // 96, 96
+    xin = x.reshape(L, N).cpu().numpy()
+    c1 = xin.reshape(-1, q, p).transpose(0, 2, 1).reshape(-1, q)
+    r1, mism, _ = ref.stage32(c1, ref.table_q(q, -1, C.SIGMA_F_EXP_FP32), None, use_crt=True)
+    assert mism == 0
+    r1 = r1.reshape(-1, p, q).transpose(0, 2, 1).reshape(-1, N)
+    got = out.reshape(L, N).cpu().numpy()
+    assert same_bits(got, r1), report(got, r1)
