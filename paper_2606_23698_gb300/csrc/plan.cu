@@ -1121,6 +1121,8 @@ extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, vo
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
         obfft_status st = OBFFT_OK;
         const size_t eb = elem_bytes(p->mode);
+        if (p->groups.empty())  // a one-grid plan: its own scratch
+            st = exec_grid(p, p->grids[0], p->batch, ins[0], outs[0], dir, p->capture_stream, p->scratch);
         for (size_t j = 0; j < p->groups.size() && st == OBFFT_OK; j++) {
             const std::vector<int> &grp = p->groups[j];
             const GridDesc &gd = p->grids[grp[0]];

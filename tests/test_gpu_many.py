@@ -72,3 +72,25 @@ print("splits", sp)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "splits" in r.stdout
+
+
+def test_many_single_grid_and_all_identical_grids():
+    """Edge cases of the grouping: a plan of one grid, a plan whose grids all
+    share one shape (one batched group), and exec_many on a one-grid plan made
+    by obfft_plan_create."""
+    from paper_2606_23698_gb300 import Plan, PlanMany, _lib
+    d = (8, 12, 16)
+    for dims in ([d], [d, d, d]):
+        xs = [S.complex_gaussian(40 + i, d).to("cuda") for i in range(len(dims))]
+        outs = PlanMany(dims, mode="fp8").exec(xs, dir=-1)
+        torch.cuda.synchronize()
+        for x, o in zip(xs, outs):
+            ref = Plan(*d, mode="fp8").exec(x, dir=-1)
+            torch.cuda.synchronize()
+            assert bits_equal(o.cpu().numpy(), ref.cpu().numpy()), dims
+    pl = Plan(*d, mode="fp8")
+    x = S.complex_gaussian(50, d).to("cuda")
+    y = torch.empty_like(x)
+    _lib.obfft_exec_many(pl.handle, [x.data_ptr()], [y.data_ptr()], -1, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert bits_equal(y.cpu().numpy(), pl.exec(x, dir=-1).cpu().numpy())
