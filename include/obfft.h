@@ -224,7 +224,9 @@ obfft_status obfft_host_crt_constants32(uint32_t *moduli, uint8_t *u_slices, uin
  * obfft_ablation_residues: canonical residues x~ mod m_k of the 12 moduli.
  * xt: device int64 [n_unique], |x~| < 2^53; variant 0 = the stage kernels'
  * 20/20/16-bit pieces with Barrett, 1 = dp4a over the bytes of x~ + 2^55,
- * 2 = 64-bit remainder.
+ * 2 = 64-bit remainder, 3 = dp4a followed by the H0 reduction (fold-and-add
+ * t -> (t >> a) c + (t mod 2^a) for the seven moduli m = 2^a - c with small c,
+ * Barrett for the other five; the co-design ladder's rung H0).
  * Both: item i < n_total uses input i mod n_unique, computed `reps` times
  * (reps >= 1) with the input perturbed by the repetition index r (slice sum
  * P_0 + r, or x~ + r), so that a timing launch is bound by the arithmetic

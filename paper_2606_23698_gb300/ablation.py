@@ -1,7 +1,7 @@
 """Epilogue ablation driver: synthetic inputs and timing of the exact
 alternative forms of the Phase-B Kulisch accumulator (word widths 32, 16, 8
 against the stage kernels' grouped 64-bit form) and of the deconstruction
-residues (pieces + Barrett, dp4a, 64-bit remainder); see
+residues (pieces + Barrett, dp4a, 64-bit remainder, dp4a + H0 fold-and-add); see
 obfft_ablation_phase_b / obfft_ablation_residues in include/obfft.h.
 
 Inputs are built with the library's own CRT constants (obfft_host_crt_constants)
@@ -18,7 +18,7 @@ import torch
 from . import _lib
 
 PHASE_B_VARIANTS = (0, 32, 16, 8)
-RESIDUE_VARIANTS = (0, 1, 2)
+RESIDUE_VARIANTS = (0, 1, 2, 3)
 
 
 def crt_constants():

@@ -23,7 +23,12 @@
 //              pieces, two multiply-adds with 2^20 and 2^40 mod m, Barrett;
 //   variant 1: dp4a: the 7 bytes of x~ + 2^55 against the bytes of
 //              2^(8i) mod m (four dp4a per modulus), Barrett;
-//   variant 2: the compiler's 64-bit remainder (reference form).
+//   variant 2: the compiler's 64-bit remainder (reference form);
+//   variant 3: dp4a as in variant 1, then the paper's H0 rung (Sec. on the
+//              co-design ladder; the Rev-34 set's reduction-friendly members,
+//              Sec. "Ozaki Scheme II"): fold-and-add t -> (t >> a) c + (t mod
+//              2^a) for the seven members m = 2^a - c with small c (2039,
+//              2029, 2027; 1024; 511, 491, 487), Barrett for the other five.
 //
 // Each kernel reads n_unique inputs (small enough to stay in L2) and processes
 // n_total items, item i using input i mod n_unique, `reps` times each with the
@@ -41,6 +46,34 @@ namespace obfft {
 __constant__ ModConsts c_abl_mc;
 
 constexpr int ABL_THREADS = 256;
+
+// The modulus set as compile-time constants for the H0 variant (the fold
+// shifts and counts must be known to the compiler); checked against the
+// plan's table before every launch.
+__host__ __device__ constexpr int h0_modulus(int k) {
+    return k == 0 ? 2039 : k == 1 ? 2029 : k == 2 ? 2027 : k == 3 ? 1089 : k == 4 ? 1024 : k == 5 ? 961
+         : k == 6 ? 841 : k == 7 ? 625 : k == 8 ? 529 : k == 9 ? 511 : k == 10 ? 491 : 487;
+}
+// a of a reduction-friendly member m = 2^a - c (c <= 25), 0 for the others
+__host__ __device__ constexpr int h0_shift(int k) {
+    const int m = h0_modulus(k);
+    return m > 2000 ? 11 : (m == 1024 ? 10 : (m >= 487 && m <= 511 ? 9 : 0));
+}
+// Folds that bring the dp4a sum t <= 7 x 255 x (m - 1) below 2m: each fold
+// maps a bound T to (T >> a) c + 2^a - 1.
+__host__ __device__ constexpr int h0_folds(int k) {
+    const int a = h0_shift(k);
+    if (a == 0) return 0;
+    const uint64_t m = (uint64_t)h0_modulus(k), c = (1ull << a) - m;
+    uint64_t t = 7ull * 255ull * (m - 1);
+    int n = 0;
+    while (t >= 2 * m && n < 8) {
+        t = (t >> a) * c + ((1ull << a) - 1);
+        n++;
+    }
+    return n;
+}
+static_assert(h0_folds(0) == 2 && h0_folds(4) == 1 && h0_folds(11) == 3, "fold counts");
 
 // Kulisch accumulator of E = sum_s P_s 256^s in words of radix 2^RHO, LANES
 // words of 32 / LANES bits packed per 32-bit register (word i in register
@@ -177,6 +210,19 @@ __global__ void __launch_bounds__(ABL_THREADS) residue_ablation_kernel(const int
                 const uint32_t th = __dp4a(lo, mc.b8hi[k][0], __dp4a(hi, mc.b8hi[k][1], 0u));
                 t = tl + (th << 8);                       // < 7 x 255 x 2047 < 2^22
                 t = t - __umulhi(t, mc.barrett[k]) * m;  // [0, 2m)
+            } else if constexpr (VARIANT == 3) {
+                const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+                const uint32_t tl = __dp4a(lo, mc.b8lo[k][0], __dp4a(hi, mc.b8lo[k][1], 0u));
+                const uint32_t th = __dp4a(lo, mc.b8hi[k][0], __dp4a(hi, mc.b8hi[k][1], 0u));
+                t = tl + (th << 8);  // sum of the bytes times 2^(8i) mod m: <= 7 x 255 x (m - 1)
+                const int a = h0_shift(k);
+                if (a == 0) {
+                    t = t - __umulhi(t, mc.barrett[k]) * m;  // [0, 2m)
+                } else {
+                    const uint32_t c = (1u << a) - (uint32_t)h0_modulus(k), mask = (1u << a) - 1u;
+#pragma unroll
+                    for (int f = 0; f < h0_folds(k); f++) t = (t >> a) * c + (t & mask);  // [0, 2m) after the last
+                }
             } else {
                 t = (uint32_t)(v % m);
             }
@@ -200,6 +246,8 @@ __global__ void __launch_bounds__(ABL_THREADS) residue_ablation_kernel(const int
 }
 
 static cudaError_t abl_upload() {
+    for (int k = 0; k < NMOD; k++)
+        if (h0_modulus(k) != kModuli[k]) return cudaErrorInvalidValue;
     ModConsts mc;
     make_mod_consts(&mc);
     return cudaMemcpyToSymbol(c_abl_mc, &mc, sizeof(mc));
@@ -237,6 +285,7 @@ cudaError_t launch_residue_ablation(int variant, int64_t n_unique, int64_t n_tot
         case 0: residue_ablation_kernel<0><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, reps, res, checksum); break;
         case 1: residue_ablation_kernel<1><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, reps, res, checksum); break;
         case 2: residue_ablation_kernel<2><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, reps, res, checksum); break;
+        case 3: residue_ablation_kernel<3><<<nb, ABL_THREADS, 0, s>>>(xt, n_unique, n_total, reps, res, checksum); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

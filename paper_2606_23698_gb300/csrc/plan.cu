@@ -1248,7 +1248,7 @@ extern "C" obfft_status obfft_ablation_phase_b(int variant, int64_t n_unique, in
 
 extern "C" obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_total, int reps,
                                                const void *xt, void *res, void *checksum, void *stream) {
-    if (variant < 0 || variant > 2) return set_error(OBFFT_ERR_ARG, "variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 3) return set_error(OBFFT_ERR_ARG, "variant must be 0, 1, 2 or 3");
     if (n_unique < 1 || n_total < 0 || reps < 1 || !xt || !checksum) return set_error(OBFFT_ERR_ARG, "bad argument");
     cudaError_t e = launch_residue_ablation(variant, n_unique, n_total, reps, (const int64_t *)xt, (uint16_t *)res,
                                             (unsigned long long *)checksum, (cudaStream_t)stream);

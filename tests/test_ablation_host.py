@@ -7,6 +7,8 @@ import math
 import numpy as np
 import pytest
 
+from oracle import constants as C
+
 S_RAW = 15
 P_BITS = 23                    # every slice sum P_s < 2^23
 LAYOUTS = {32: 28, 16: 12, 8: 6}  # word width -> radix bits (rho)
@@ -82,3 +84,29 @@ def test_packed_deposit_and_sweep_are_exact(wb):
             carry = t >> rho
             E |= (t & ((1 << rho) - 1)) << (rho * i)
         assert E % 2 ** 128 == sum(p << (8 * s) for s, p in enumerate(P)) % 2 ** 128
+
+
+# The H0 residue form (fold-and-add for the pseudo-Mersenne members of the
+# modulus set, Sec. "Ozaki Scheme II" and the co-design ladder's rung H0): the
+# paper names the seven friendly members, and the folds the kernel applies
+# (two for a = 11, one for 1024, three for a = 9 from the dp4a bound
+# 7 x 255 x (m - 1)) must leave every possible sum below 2m and congruent to it.
+H0_FRIENDLY = {2039: (11, 2), 2029: (11, 2), 2027: (11, 2), 1024: (10, 1), 511: (9, 2), 491: (9, 3), 487: (9, 3)}
+
+
+def test_h0_friendly_members_are_the_papers_seven():
+    friendly = [m for m in C.MODULI if any(m == (1 << a) - c for a in (9, 10, 11) for c in range(0, 26))]
+    assert sorted(friendly) == sorted(H0_FRIENDLY)
+    assert len(friendly) == 7
+
+
+@pytest.mark.parametrize("m", sorted(H0_FRIENDLY))
+def test_h0_folds_reach_two_m_exhaustively(m):
+    a, folds = H0_FRIENDLY[m]
+    c = (1 << a) - m
+    t0 = np.arange(0, 7 * 255 * (m - 1) + 1, dtype=np.int64)
+    t = t0.copy()
+    for _ in range(folds):
+        t = (t >> a) * c + (t & ((1 << a) - 1))
+    assert int(t.max()) < 2 * m
+    assert np.array_equal(t % m, t0 % m)

@@ -85,7 +85,7 @@ def test_residue_forms_exact():
     want = np.array([[x % m for m in C.MODULI] for x in xs], np.uint16)
     dx = torch.tensor(xs, dtype=torch.int64, device="cuda")
     sums = set()
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         res = torch.empty((n, 12), dtype=torch.int16, device="cuda")
         ck = torch.zeros(1, dtype=torch.int64, device="cuda")
         _lib.obfft_ablation_residues(variant, n, n, dx.data_ptr(), res.data_ptr(), ck.data_ptr())
@@ -101,4 +101,4 @@ def test_ablation_argument_errors():
     with pytest.raises(_lib.ObfftError):
         _lib.obfft_ablation_phase_b(12, 1, 1, 0, 0, None, 0)
     with pytest.raises(_lib.ObfftError):
-        _lib.obfft_ablation_residues(3, 1, 1, 0, None, 0)
+        _lib.obfft_ablation_residues(4, 1, 1, 0, None, 0)
