@@ -121,7 +121,9 @@ obfft_status obfft_plan_create_many(obfft_plan *out, int count, const int64_t *d
  * (arrays of `count` pointers in HOST memory).  Asynchronous on `stream`.
  * The work (per group: device-to-device gathers of the members, six batched
  * stage launches, scatters of the results) is captured once into a CUDA
- * graph per set of pointers and direction, and replayed by later calls.
+ * graph per set of pointers and direction, and replayed by later calls.  The
+ * groups are independent branches of the graph, so their launches can run
+ * concurrently.
  */
 obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, void *const *outs, int dir,
                              void *stream);

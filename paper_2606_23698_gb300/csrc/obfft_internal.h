@@ -130,6 +130,11 @@ struct obfft_plan_s {
     // result buffer (all offsets into `scratch`).
     std::vector<std::vector<int>> groups;
     std::vector<void *> group_in, group_out, group_scratch;
+    // the groups' launch chains are captured on streams of their own, forked
+    // from and joined back into the capture stream, so the graph runs them as
+    // parallel branches (one stream and one join event per group)
+    std::vector<cudaStream_t> group_streams;
+    std::vector<cudaEvent_t> group_events;  // [0]: fork, [1 + j]: join of group j
     // host-to-host execution: two grid-sized device buffers, a copy stream and
     // its events, created on the first obfft_exec_host call
     void *host_io[2] = {nullptr, nullptr};

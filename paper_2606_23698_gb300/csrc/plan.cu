@@ -861,6 +861,8 @@ extern "C" obfft_status obfft_destroy(obfft_plan p) {
     free_tables(p);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+    for (cudaStream_t gs : p->group_streams) cudaStreamDestroy(gs);
+    for (cudaEvent_t ev : p->group_events) cudaEventDestroy(ev);
     if (p->copy_stream) cudaStreamSynchronize(p->copy_stream), cudaStreamDestroy(p->copy_stream);
     for (cudaEvent_t ev : p->copy_events) cudaEventDestroy(ev);
     cudaFree(p->host_io[0]);
@@ -1116,6 +1118,16 @@ extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, vo
         }
         cudaError_t e = cudaSuccess;
         if (!p->capture_stream) e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking);
+        while (e == cudaSuccess && p->group_streams.size() < p->groups.size()) {
+            cudaStream_t gs = nullptr;
+            e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) p->group_streams.push_back(gs);
+        }
+        while (e == cudaSuccess && p->group_events.size() < p->groups.size() + 1) {
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) p->group_events.push_back(ev);
+        }
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, cudaGetErrorString(e));
         e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
@@ -1123,24 +1135,38 @@ extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, vo
         const size_t eb = elem_bytes(p->mode);
         if (p->groups.empty())  // a one-grid plan: its own scratch
             st = exec_grid(p, p->grids[0], p->batch, ins[0], outs[0], dir, p->capture_stream, p->scratch);
+        else
+            st = cuda_err(cudaEventRecord(p->group_events[0], p->capture_stream), "fork");
+        size_t forked = 0;  // groups whose stream joined the capture
         for (size_t j = 0; j < p->groups.size() && st == OBFFT_OK; j++) {
             const std::vector<int> &grp = p->groups[j];
             const GridDesc &gd = p->grids[grp[0]];
+            cudaStream_t gs = p->group_streams[j];
+            st = cuda_err(cudaStreamWaitEvent(gs, p->group_events[0], 0), "fork");
+            if (st != OBFFT_OK) break;
+            forked = j + 1;
             if (grp.size() == 1) {
-                st = exec_grid(p, gd, 1, ins[grp[0]], outs[grp[0]], dir, p->capture_stream, p->group_scratch[j]);
+                st = exec_grid(p, gd, 1, ins[grp[0]], outs[grp[0]], dir, gs, p->group_scratch[j]);
                 continue;
             }
             // gather the members into one batch, transform, scatter the results
             const size_t bytes = (size_t)(gd.n[0] * gd.n[1] * gd.n[2]) * eb;
             for (size_t i = 0; i < grp.size() && st == OBFFT_OK; i++)
                 st = cuda_err(cudaMemcpyAsync((char *)p->group_in[j] + i * bytes, ins[grp[i]], bytes,
-                                              cudaMemcpyDeviceToDevice, p->capture_stream), "gather");
+                                              cudaMemcpyDeviceToDevice, gs), "gather");
             if (st == OBFFT_OK)
-                st = exec_grid(p, gd, (int64_t)grp.size(), p->group_in[j], p->group_out[j], dir, p->capture_stream,
+                st = exec_grid(p, gd, (int64_t)grp.size(), p->group_in[j], p->group_out[j], dir, gs,
                                p->group_scratch[j]);
             for (size_t i = 0; i < grp.size() && st == OBFFT_OK; i++)
                 st = cuda_err(cudaMemcpyAsync(outs[grp[i]], (char *)p->group_out[j] + i * bytes, bytes,
-                                              cudaMemcpyDeviceToDevice, p->capture_stream), "scatter");
+                                              cudaMemcpyDeviceToDevice, gs), "scatter");
+        }
+        // join every forked branch back into the capture stream (also after an
+        // error, so that the capture can end cleanly)
+        for (size_t j = 0; j < forked; j++) {
+            cudaError_t ej = cudaEventRecord(p->group_events[1 + j], p->group_streams[j]);
+            if (ej == cudaSuccess) ej = cudaStreamWaitEvent(p->capture_stream, p->group_events[1 + j], 0);
+            if (st == OBFFT_OK && ej != cudaSuccess) st = cuda_err(ej, "join");
         }
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(p->capture_stream, &graph);
