@@ -475,6 +475,22 @@ static void fill_matrices(AxisTables &t, int sexp) {
             }
 }
 
+// Stages with K <= 16 run two lines per TMEM lane in the tcgen05 stage kernel
+// (FP8 and FP16-carrier modes): their constant operand is the block-diagonal
+// 32 x 32 matrix with the K x K matrix of each group at rows and columns 0
+// and 16, zero elsewhere.
+static std::vector<int64_t> pair_blocks(const std::vector<int64_t> &F, int groups, int K) {
+    std::vector<int64_t> P((size_t)groups * 32 * 32 * 2, 0);
+    for (int g = 0; g < groups; g++)
+        for (int b = 0; b < 2; b++)
+            for (int n = 0; n < K; n++)
+                for (int j = 0; j < K; j++)
+                    for (int c = 0; c < 2; c++)
+                        P[(((size_t)g * 32 + 16 * b + n) * 32 + 16 * b + j) * 2 + c] =
+                            F[(((size_t)g * K + n) * K + j) * 2 + c];
+    return P;
+}
+
 static cudaError_t upload(const void *host, size_t bytes, void **dev) {
     cudaError_t e = cudaMalloc(dev, bytes);
     if (e != cudaSuccess) return e;
@@ -494,15 +510,19 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
     } else if (P->mode == OBFFT_MODE_FP8) {
         e = fp8_upload_constants();
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP8 constants: ") + cudaGetErrorString(e));
-        std::vector<uint8_t> s1 = build_fp8_planes(t.Fq, 1, t.q);
-        std::vector<uint8_t> s2 = build_fp8_planes(t.Fp, t.q, t.p);
+        std::vector<uint8_t> s1 = t.q <= 16 ? build_fp8_planes(pair_blocks(t.Fq, 1, t.q), 1, 32)
+                                            : build_fp8_planes(t.Fq, 1, t.q);
+        std::vector<uint8_t> s2 = t.p <= 16 ? build_fp8_planes(pair_blocks(t.Fp, t.q, t.p), t.q, 32)
+                                            : build_fp8_planes(t.Fp, t.q, t.p);
         e = upload(s1.data(), s1.size(), &t.fp8_s1);
         if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
     } else if (P->mode == OBFFT_MODE_FP16) {
         e = fp8_upload_constants();
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP16 constants: ") + cudaGetErrorString(e));
-        std::vector<uint8_t> s1 = build_fp16_planes(t.Fq, 1, t.q, kModuli, NMOD);
-        std::vector<uint8_t> s2 = build_fp16_planes(t.Fp, t.q, t.p, kModuli, NMOD);
+        std::vector<uint8_t> s1 = t.q <= 16 ? build_fp16_planes(pair_blocks(t.Fq, 1, t.q), 1, 32, kModuli, NMOD)
+                                            : build_fp16_planes(t.Fq, 1, t.q, kModuli, NMOD);
+        std::vector<uint8_t> s2 = t.p <= 16 ? build_fp16_planes(pair_blocks(t.Fp, t.q, t.p), t.q, 32, kModuli, NMOD)
+                                            : build_fp16_planes(t.Fp, t.q, t.p, kModuli, NMOD);
         e = upload(s1.data(), s1.size(), &t.fp8_s1);
         if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
     } else if (P->mode == OBFFT_MODE_FP32) {

@@ -1,7 +1,8 @@
 // FP8-mode Bailey stage on Blackwell tensor cores (tcgen05, sm_103a).
 //
 // One CTA transforms 128 columns (one Ozaki-II complex GEMM per column,
-// Algorithm 1, one half).  Per modulus m_k:
+// Algorithm 1, one half), or 256 when K <= 16 (two columns per TMEM lane, see
+// the kernel's LPV parameter).  Per modulus m_k:
 //   * the data residues (x~ mod m_k, balanced) of the real and
 //     imaginary parts are split into E4M3-exact digit planes by the SIMT
 //     threads and written straight into tensor memory, where tcgen05.mma reads
@@ -295,7 +296,7 @@ __device__ __forceinline__ void epilogue_modulus(uint32_t tacc_re, uint32_t tacc
     }
 }
 
-// Input tile of the columns [cb, cb + 128): stage 1 reads whole or partial
+// Input tile of the columns [cb, cb + width): stage 1 reads whole or partial
 // lines, one contiguous range [e0, e1) of elements; stage 2 reads K = p
 // contiguous elements per column, at addresses in arithmetic progression.
 struct InputTile {
@@ -303,10 +304,10 @@ struct InputTile {
     int64_t src0, n;   // stage 2: column i starts at element src0 + i n
     int nvalid;        // stage 2: valid columns (the first nvalid of the tile)
 };
-__device__ __forceinline__ InputTile input_tile(const ColMapT &map, int64_t ncols, int64_t cb) {
+__device__ __forceinline__ InputTile input_tile(const ColMapT &map, int64_t ncols, int64_t cb, int width) {
     InputTile t;
     if (map.stage == 1) {
-        const int64_t l0 = cb / map.p, l1 = min(cb + 127, ncols - 1) / map.p;
+        const int64_t l0 = cb / map.p, l1 = min(cb + width - 1, ncols - 1) / map.p;
         t.e0 = l0 * map.n;
         t.e1 = (l1 + 1) * map.n;
         t.src0 = 0;
@@ -317,7 +318,7 @@ __device__ __forceinline__ InputTile input_tile(const ColMapT &map, int64_t ncol
         t.e0 = t.e1 = 0;
         t.src0 = l0 * map.n + k2 * map.p;
         t.n = map.n;
-        t.nvalid = (int)max((int64_t)0, min((int64_t)128, map.L - l0));
+        t.nvalid = (int)max((int64_t)0, min((int64_t)width, map.L - l0));
     }
     return t;
 }
@@ -379,7 +380,13 @@ struct CarrierCfg {
     __host__ __device__ static constexpr int planes_of(int k) { return CAR ? 8 : 4 * fp8_ndig(k); }
 };
 
-template <int NPAD, int CAR>
+// LPV = 2 (stages with K <= 16, NPAD = 32): every TMEM lane carries two DFT
+// columns (lines) side by side, line h in slots [16 h, 16 h + 16) of the 32
+// element and output slots, with a block-diagonal constant matrix (the K x K
+// matrix at rows and columns 0 and 16).  Threads with qd < 2 work on line 0,
+// the others on line 1, so every thread still deconstructs, reduces and
+// finishes elements of one line only; a CTA covers 256 lines.
+template <int NPAD, int CAR, int LPV>
 __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     stage_fp8_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab,
                      const ModConsts *__restrict__ gmc, ColMapT map, int64_t ncols, int K, int Kout,
@@ -401,12 +408,16 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // reads a slot that another thread may still be writing
     __shared__ int fail[2];
 
+    static_assert(NPAD == 32 && (LPV == 1 || LPV == 2), "32 slots per lane, one or two lines");
+    constexpr int TILE = 128 * LPV;        // columns (lines) per CTA
+    constexpr int KS = NPAD / LPV;         // slots of one line
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int sub = w & 3, qd = w >> 2;
     const int c = 32 * sub + lane;
+    const int hl = LPV == 1 ? 0 : (qd >> 1);  // this thread's line within its lane
     const uint32_t lanebase = (uint32_t)(32 * sub) << 16;
-    const int64_t cbase = (int64_t)blockIdx.x * 128;
-    const int64_t cg = cbase + c;
+    const int64_t cbase = (int64_t)blockIdx.x * TILE;
+    const int64_t cg = cbase + 128 * hl + c;
     const bool cvalid = map.valid(cg, ncols);
     const int group = map.group(cbase);
 
@@ -434,7 +445,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     if (w == 0) {
         tmem_alloc(smem_u32(&tmem_holder), 512);
     } else if (w == 1) {
-        const InputTile itile = input_tile(map, ncols, cbase);
+        const InputTile itile = input_tile(map, ncols, cbase, TILE);
         if (lane == 0) {
             abort_flag = 0;
             if (CAR) fail[0] = fail[1] = 0;
@@ -457,7 +468,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         // the tile about one wave of CTAs ahead, most likely next on some SM
         const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
         if (pf_ahead > 0 && nb < (int64_t)gridDim.x)
-            prefetch_input_tile(map, input_tile(map, ncols, nb * 128), K, in, lane);
+            prefetch_input_tile(map, input_tile(map, ncols, nb * TILE, TILE), K, in, lane);
     } else if (w == 3 && !CAR) {
         reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[lane] = 0u;
     }
@@ -476,18 +487,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             else
                 tmem_st4_const(ta, 0u);
         }
-    // K <= 16: bytes 16..31 of every A row stay zero (columns 4..7 of each of the 6 planes)
-    if (NPAD == 16 && qd == 0 && !CAR) {
-#pragma unroll
-        for (int b = 0; b < (int)N_ABUF; b++)
-#pragma unroll
-            for (int d = 0; d < 6; d++) {
-                uint32_t ta = tmem + lanebase + APL_BASE + b * APL_COLS + d * 8 + 4;
-                tmem_st2(ta, 0u, 0u);
-                tmem_st2(ta + 2, 0u, 0u);
-            }
-    }
-
     // ---------------- deconstruction of this thread's EPT elements ----------------
     Pieces pR[EPT], pI[EPT];
     int e;
@@ -497,13 +496,13 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const bool okin = mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
         if (!okin) atomicExch(&abort_flag, 1);
         // element j of this column at sIn + (sbase + j sstride) * 16
-        const int64_t sbase = map.stage == 1 ? ibase - s_e0 : (int64_t)c * (K + 1);
+        const int64_t sbase = map.stage == 1 ? ibase - s_e0 : (int64_t)(128 * hl + c) * (K + 1);
         const int64_t sstride = map.stage == 1 ? istride : 1;
         uint64_t xb[EPT][2];
         int lead = LEAD_ZERO;
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
-            int j = EPT * qd + jj;
+            int j = EPT * qd + jj - KS * hl;
             double2 x = make_double2(0.0, 0.0);
             if (okin && cvalid && j < K)
                 x = *reinterpret_cast<const double2 *>(sIn + (sbase + (int64_t)j * sstride) * 16);
@@ -513,7 +512,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         }
         colpart[qd][c] = lead;
         __syncthreads();
-        int l2 = max(max(colpart[0][c], colpart[1][c]), max(colpart[2][c], colpart[3][c]));
+        int l2 = LPV == 1 ? max(max(colpart[0][c], colpart[1][c]), max(colpart[2][c], colpart[3][c]))
+                          : max(colpart[2 * hl][c], colpart[2 * hl + 1][c]);
         e = l2 == LEAD_ZERO ? 0 : l2;
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
@@ -766,7 +766,16 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             double im = kulisch_pack_fp8_fast(wv + 21, mc, e - 104, ebias, zbias, slow_im, Rim, near_im);
             if (slow_re) re = kulisch_finish_slow(Rre[0], Rre[1], Rre[2], Rre[3], near_re, e - 104);
             if (slow_im) im = kulisch_finish_slow(Rim[0], Rim[1], Rim[2], Rim[3], near_im, e - 104);
-            if (cvalid && kout < Kout) out[obase + (int64_t)kout * ostride] = make_double2(re, im);
+            const int kl = kout - KS * hl;  // the output index within this thread's line
+            if (cvalid && kl < (LPV == 1 ? Kout : K)) out[obase + (int64_t)kl * ostride] = make_double2(re, im);
+        };
+        // output slot of row block bi of the wave starting at b0.  LPV = 2: the
+        // wave's blocks 0, 1 and 4, 5 are outputs of line 0 and blocks 2, 3 and
+        // 6, 7 of line 1 (4 consecutive outputs of each line per wave), so the
+        // thread that finishes blocks qd and qd + 4 stays on its own line
+        auto kout_of = [&](int b0, int bi) -> int {
+            if constexpr (LPV == 1) return b0 + bi;
+            else return KS * ((bi & 3) >> 1) + (b0 >> 1) + 2 * (bi >> 2) + (bi & 1);
         };
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
             const int nb = min(per_wave, Kout - b0);
@@ -776,14 +785,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             // group is finished; every thread waits once on each barrier per wave
             if (tid == 0) {
                 tc_fence_after();
-                // descriptors advance by the 16-byte-unit offset of the next row block
-                uint64_t ad = adescA + (uint64_t)((uint32_t)b0 * (16 * PA_ROWB / 16));
+                // a row block's descriptor lies 16 x PA_ROWB bytes (in 16-byte
+                // units) per output slot past the staging start
                 uint32_t d = tmem;
                 const int na = min(nb, 4);
                 for (int bi = 0; bi < nb; bi++) {
+                    const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b0, bi) * (16 * PA_ROWB / 16));
                     tc_mma_f16(d, ad, bdescA0, idescA, 1);
                     tc_mma_f16(d, ad + 16, bdescA1, idescA, 1);  // + 256 bytes: K 16..31
-                    ad += 16 * PA_ROWB / 16;
                     d += PA_N;
                     if (bi == na - 1) tc_commit(smem_u32(&mbar[2]));
                 }
@@ -796,7 +805,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 tmem_wait_ld();
                 after_wait(wv);
                 if (bi < nb_next) preset(bi);
-                finish(wv, b0 + bi);
+                finish(wv, kout_of(b0, bi));
             };
             const bool okA = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
             mph[0] ^= 1u;
@@ -871,37 +880,41 @@ static size_t fp16_smem_bytes(int Kout, int npad) {
 template <int CAR>
 static cudaError_t launch_stage_carrier(const AxisTables &t, const void *pab, int *status, const StageGeom &g,
                                         int stage, const double2 *in, double2 *out, cudaStream_t s) {
+    const int K = stage == 1 ? g.q : g.p;
+    if (K > 32) return cudaErrorInvalidValue;
+    // K <= 16: two lines per TMEM lane (the constant planes are block-diagonal
+    // 32 x 32, built that way by the plan), 256 lines per CTA, all 32 output
+    // slots through the staging and Phase A
+    const int lpv = K <= 16 ? 2 : 1, tile = 128 * lpv;
+    const int kslots = lpv == 2 ? 32 : K;
     ColMapT map;
     map.stage = stage;
     map.L = g.L;
-    map.Lpad = (g.L + 127) / 128 * 128;
+    map.Lpad = (g.L + tile - 1) / tile * tile;
     map.P = g.P;
     map.n = g.n;
     map.p = g.p;
     map.q = g.q;
-    const int K = stage == 1 ? g.q : g.p;
-    if (K > 32) return cudaErrorInvalidValue;
-    const int npad = K <= 16 ? 16 : 32;
     const int64_t ncols = stage == 1 ? g.L * g.p : map.Lpad * g.q;
     const uint8_t *planes = (const uint8_t *)(stage == 1 ? t.fp8_s1 : t.fp8_s2);
-    const size_t smem = CAR ? fp16_smem_bytes(K, npad) : fp8_smem_bytes(K, npad);
-    int64_t blocks = (ncols + 127) / 128;
+    const size_t smem = CAR ? fp16_smem_bytes(kslots, 32) : fp8_smem_bytes(kslots, 32);
+    int64_t blocks = (ncols + tile - 1) / tile;
     if (blocks == 0) return cudaSuccess;
     int dev = 0, nsm = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    if (npad == 16) {
-        err = cudaFuncSetAttribute(stage_fp8_kernel<16, CAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (lpv == 2) {
+        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp8_kernel<16, CAR><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, nullptr, map, ncols, K, K, in, out, status, nsm);
+        stage_fp8_kernel<32, CAR, 2><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, nullptr, map, ncols, K, kslots, in, out, status, nsm);
     } else {
-        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp8_kernel<32, CAR><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, nullptr, map, ncols, K, K, in, out, status, nsm);
+        stage_fp8_kernel<32, CAR, 1><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, nullptr, map, ncols, K, kslots, in, out, status, nsm);
     }
     return cudaGetLastError();
 }
