@@ -91,7 +91,12 @@ struct AxisTables {
     void *int8_s1 = nullptr, *int8_s2 = nullptr;
     size_t int8_s1_bytes = 0, int8_s2_bytes = 0;
     // FP8 mode: E4M3 digit planes of the constant matrices, stage 1 / stage 2
+    // (FP16-carrier and FP32 modes: their FP16 planes), laid out for
+    // fp8_lines_per_lane(K) lines per TMEM lane; stages with K <= 8 also get
+    // planes for two lines per lane (the launch picks the layout that needs
+    // fewer rounds of CTAs)
     void *fp8_s1 = nullptr, *fp8_s2 = nullptr;
+    void *fp8_s1_l2 = nullptr, *fp8_s2_l2 = nullptr;
     // native comparators: twiddles exp(dir 2 pi i m / n) for m < n, then the
     // q and p tables, as double pairs (FP64) or float pairs (FP32)
     void *tw = nullptr;
@@ -171,6 +176,10 @@ std::vector<uint8_t> build_phase_a_b32();
 cudaError_t launch_stage_native32(const AxisTables &t, const StageGeom &g, int stage, const float2 *in,
                                   float2 *out, cudaStream_t s);
 size_t fp8_smem_bytes(int Kout, int npad);
+// Lines per TMEM lane of the tcgen05 stage kernel (FP8 and FP16-carrier
+// modes) for a DFT of length K <= 32: the 32 element and output slots of a
+// lane hold 4 lines of up to 8, 2 of up to 16, or 1 of up to 32.
+inline int fp8_lines_per_lane(int K) { return K <= 8 ? 4 : (K <= 16 ? 2 : 1); }
 cudaError_t fp8_upload_constants();  // once per device, outside any stream capture
 cudaError_t launch_bounded_wait_selftest(int *status, cudaStream_t s);
 std::vector<uint8_t> build_fp8_planes(const std::vector<int64_t> &F, int groups, int K);

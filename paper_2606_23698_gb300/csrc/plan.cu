@@ -475,18 +475,19 @@ static void fill_matrices(AxisTables &t, int sexp) {
             }
 }
 
-// Stages with K <= 16 run two lines per TMEM lane in the tcgen05 stage kernel
-// (FP8 and FP16-carrier modes): their constant operand is the block-diagonal
-// 32 x 32 matrix with the K x K matrix of each group at rows and columns 0
-// and 16, zero elsewhere.
-static std::vector<int64_t> pair_blocks(const std::vector<int64_t> &F, int groups, int K) {
+// Stages with K <= 16 run lpv > 1 lines per TMEM lane in the tcgen05 stage
+// kernel (FP8 and FP16-carrier modes): their constant operand is the
+// block-diagonal 32 x 32 matrix with the K x K matrix of each group at rows
+// and columns 32 b / lpv (b < lpv), zero elsewhere.
+static std::vector<int64_t> lane_blocks(const std::vector<int64_t> &F, int groups, int K, int lpv) {
+    const int ks = 32 / lpv;
     std::vector<int64_t> P((size_t)groups * 32 * 32 * 2, 0);
     for (int g = 0; g < groups; g++)
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < lpv; b++)
             for (int n = 0; n < K; n++)
                 for (int j = 0; j < K; j++)
                     for (int c = 0; c < 2; c++)
-                        P[(((size_t)g * 32 + 16 * b + n) * 32 + 16 * b + j) * 2 + c] =
+                        P[(((size_t)g * 32 + ks * b + n) * 32 + ks * b + j) * 2 + c] =
                             F[(((size_t)g * K + n) * K + j) * 2 + c];
     return P;
 }
@@ -495,6 +496,25 @@ static cudaError_t upload(const void *host, size_t bytes, void **dev) {
     cudaError_t e = cudaMalloc(dev, bytes);
     if (e != cudaSuccess) return e;
     return cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice);
+}
+
+// Constant planes of both stages for the tcgen05 stage kernel: the layout for
+// fp8_lines_per_lane(K) lines per lane, and for K <= 8 also the two-line one.
+template <typename Build>
+static cudaError_t upload_planes(AxisTables &t, Build build) {
+    const int lq = fp8_lines_per_lane(t.q), lp = fp8_lines_per_lane(t.p);
+    std::vector<uint8_t> s1 = build(t.Fq, 1, t.q, lq), s2 = build(t.Fp, t.q, t.p, lp);
+    cudaError_t e = upload(s1.data(), s1.size(), &t.fp8_s1);
+    if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
+    if (e == cudaSuccess && lq == 4) {
+        s1 = build(t.Fq, 1, t.q, 2);
+        e = upload(s1.data(), s1.size(), &t.fp8_s1_l2);
+    }
+    if (e == cudaSuccess && lp == 4) {
+        s2 = build(t.Fp, t.q, t.p, 2);
+        e = upload(s2.data(), s2.size(), &t.fp8_s2_l2);
+    }
+    return e;
 }
 
 static obfft_status build_tables(obfft_plan P, AxisTables &t) {
@@ -510,21 +530,16 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
     } else if (P->mode == OBFFT_MODE_FP8) {
         e = fp8_upload_constants();
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP8 constants: ") + cudaGetErrorString(e));
-        std::vector<uint8_t> s1 = t.q <= 16 ? build_fp8_planes(pair_blocks(t.Fq, 1, t.q), 1, 32)
-                                            : build_fp8_planes(t.Fq, 1, t.q);
-        std::vector<uint8_t> s2 = t.p <= 16 ? build_fp8_planes(pair_blocks(t.Fp, t.q, t.p), t.q, 32)
-                                            : build_fp8_planes(t.Fp, t.q, t.p);
-        e = upload(s1.data(), s1.size(), &t.fp8_s1);
-        if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
+        e = upload_planes(t, [&](const std::vector<int64_t> &F, int groups, int K, int lpv) {
+            return lpv > 1 ? build_fp8_planes(lane_blocks(F, groups, K, lpv), groups, 32) : build_fp8_planes(F, groups, K);
+        });
     } else if (P->mode == OBFFT_MODE_FP16) {
         e = fp8_upload_constants();
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP16 constants: ") + cudaGetErrorString(e));
-        std::vector<uint8_t> s1 = t.q <= 16 ? build_fp16_planes(pair_blocks(t.Fq, 1, t.q), 1, 32, kModuli, NMOD)
-                                            : build_fp16_planes(t.Fq, 1, t.q, kModuli, NMOD);
-        std::vector<uint8_t> s2 = t.p <= 16 ? build_fp16_planes(pair_blocks(t.Fp, t.q, t.p), t.q, 32, kModuli, NMOD)
-                                            : build_fp16_planes(t.Fp, t.q, t.p, kModuli, NMOD);
-        e = upload(s1.data(), s1.size(), &t.fp8_s1);
-        if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
+        e = upload_planes(t, [&](const std::vector<int64_t> &F, int groups, int K, int lpv) {
+            return lpv > 1 ? build_fp16_planes(lane_blocks(F, groups, K, lpv), groups, 32, kModuli, NMOD)
+                           : build_fp16_planes(F, groups, K, kModuli, NMOD);
+        });
     } else if (P->mode == OBFFT_MODE_FP32) {
         e = fp32_upload_constants();
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP32 constants: ") + cudaGetErrorString(e));
@@ -605,6 +620,8 @@ static void free_tables(obfft_plan P) {
         cudaFree(t.int8_s2);
         cudaFree(t.fp8_s1);
         cudaFree(t.fp8_s2);
+        cudaFree(t.fp8_s1_l2);
+        cudaFree(t.fp8_s2_l2);
         cudaFree(t.tw);
     }
     P->tables.clear();
@@ -674,6 +691,7 @@ static float time_split(obfft_plan P, int n, int pp, int qq, void *buf, void *tm
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(t.int8_s1); cudaFree(t.int8_s2); cudaFree(t.fp8_s1); cudaFree(t.fp8_s2); cudaFree(t.tw);
+    cudaFree(t.fp8_s1_l2); cudaFree(t.fp8_s2_l2);
     return best;
 }
 

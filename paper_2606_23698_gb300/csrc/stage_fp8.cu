@@ -410,12 +410,13 @@ struct CarrierCfg {
     __host__ __device__ static constexpr int planes_of(int k) { return CAR ? 8 : 4 * fp8_ndig(k); }
 };
 
-// LPV = 2 (stages with K <= 16, NPAD = 32): every TMEM lane carries two DFT
-// columns (lines) side by side, line h in slots [16 h, 16 h + 16) of the 32
-// element and output slots, with a block-diagonal constant matrix (the K x K
-// matrix at rows and columns 0 and 16).  Threads with qd < 2 work on line 0,
-// the others on line 1, so every thread still deconstructs, reduces and
-// finishes elements of one line only; a CTA covers 256 lines.
+// LPV = 2 or 4 (stages with K <= 16 or K <= 8, NPAD = 32): every TMEM lane
+// carries LPV DFT columns (lines) side by side, line h in slots
+// [KS h, KS h + KS), KS = 32 / LPV, of the 32 element and output slots, with
+// a block-diagonal constant matrix (the K x K matrix at rows and columns
+// KS h).  The threads of quarter-warp group qd work on line qd / (4 / LPV),
+// so every thread still deconstructs, reduces and finishes elements of one
+// line only; a CTA covers 128 LPV lines.
 template <int NPAD, int CAR, int LPV>
 __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     stage_fp8_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab,
@@ -440,13 +441,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // reads a slot that another thread may still be writing
     __shared__ int fail[2];
 
-    static_assert(NPAD == 32 && (LPV == 1 || LPV == 2), "32 slots per lane, one or two lines");
+    static_assert(NPAD == 32 && (LPV == 1 || LPV == 2 || LPV == 4), "32 slots per lane, 1, 2 or 4 lines");
+    constexpr int QPL = 4 / LPV;           // quarter-warp groups per line
     constexpr int TILE = 128 * LPV;        // columns (lines) per CTA
     constexpr int KS = NPAD / LPV;         // slots of one line
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int sub = w & 3, qd = w >> 2;
     const int c = 32 * sub + lane;
-    const int hl = LPV == 1 ? 0 : (qd >> 1);  // this thread's line within its lane
+    const int hl = qd / QPL;  // this thread's line within its lane
     const uint32_t lanebase = (uint32_t)(32 * sub) << 16;
     const int64_t cbase = (int64_t)blockIdx.x * TILE;
     const int64_t cg = cbase + 128 * hl + c;
@@ -546,8 +548,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         }
         colpart[qd][c] = lead;
         __syncthreads();
-        int l2 = LPV == 1 ? max(max(colpart[0][c], colpart[1][c]), max(colpart[2][c], colpart[3][c]))
-                          : max(colpart[2 * hl][c], colpart[2 * hl + 1][c]);
+        int l2 = colpart[QPL * hl][c];
+#pragma unroll
+        for (int i = 1; i < QPL; i++) l2 = max(l2, colpart[QPL * hl + i][c]);
         e = l2 == LEAD_ZERO ? 0 : l2;
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
@@ -826,13 +829,15 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             const int kl = kout - KS * hl;  // the output index within this thread's line
             if (cvalid && kl < (LPV == 1 ? Kout : K)) out[obase + (int64_t)kl * ostride] = make_double2(re, im);
         };
-        // output slot of row block bi of the wave starting at b0.  LPV = 2: the
-        // wave's blocks 0, 1 and 4, 5 are outputs of line 0 and blocks 2, 3 and
-        // 6, 7 of line 1 (4 consecutive outputs of each line per wave), so the
-        // thread that finishes blocks qd and qd + 4 stays on its own line
+        // output slot of row block bi of the wave starting at b0.  With LPV
+        // lines per lane, block bi belongs to line (bi & 3) / QPL, so the
+        // thread that finishes blocks qd and qd + 4 stays on its own line;
+        // each wave covers 8 / LPV consecutive outputs of every line (LPV = 2:
+        // blocks 0, 1, 4, 5 are outputs 4w .. 4w + 3 of line 0)
         auto kout_of = [&](int b0, int bi) -> int {
             if constexpr (LPV == 1) return b0 + bi;
-            else return KS * ((bi & 3) >> 1) + (b0 >> 1) + 2 * (bi >> 2) + (bi & 1);
+            else if constexpr (LPV == 2) return KS * ((bi & 3) >> 1) + (b0 >> 1) + 2 * (bi >> 2) + (bi & 1);
+            else return KS * (bi & 3) + (b0 >> 2) + (bi >> 2);
         };
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
             const int nb = min(per_wave, Kout - b0);
@@ -940,30 +945,51 @@ static cudaError_t launch_stage_carrier(const AxisTables &t, const void *pab, in
                                         int stage, const double2 *in, double2 *out, cudaStream_t s) {
     const int K = stage == 1 ? g.q : g.p;
     if (K > 32) return cudaErrorInvalidValue;
-    // K <= 16: two lines per TMEM lane (the constant planes are block-diagonal
-    // 32 x 32, built that way by the plan), 256 lines per CTA, all 32 output
-    // slots through the staging and Phase A
-    const int lpv = K <= 16 ? 2 : 1, tile = 128 * lpv;
-    const int kslots = lpv == 2 ? 32 : K;
-    ColMapT map;
-    map.stage = stage;
-    map.L = g.L;
-    map.Lpad = (g.L + tile - 1) / tile * tile;
-    map.P = g.P;
-    map.n = g.n;
-    map.p = g.p;
-    map.q = g.q;
-    const int64_t ncols = stage == 1 ? g.L * g.p : map.Lpad * g.q;
-    const uint8_t *planes = (const uint8_t *)(stage == 1 ? t.fp8_s1 : t.fp8_s2);
-    const size_t smem = CAR ? fp16_smem_bytes(kslots, 32) : fp8_smem_bytes(kslots, 32);
-    int64_t blocks = (ncols + tile - 1) / tile;
-    if (blocks == 0) return cudaSuccess;
     int dev = 0, nsm = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    if (lpv == 2) {
+    // K <= 16 (K <= 8): two (four) lines per TMEM lane, 128 x lpv lines per
+    // CTA, all 32 output slots through the staging and Phase A; the constant
+    // planes are block-diagonal 32 x 32, built by the plan for
+    // fp8_lines_per_lane(K) lines and, at K <= 8, also for two.  One CTA runs
+    // per SM at a time: four lines are used only when they need fewer rounds
+    // of CTAs than two (a small launch keeps more SMs busy with two).
+    auto columns = [&](int lpv, int64_t &Lpad) {
+        const int64_t tile = 128 * lpv;
+        Lpad = (g.L + tile - 1) / tile * tile;
+        return stage == 1 ? g.L * g.p : Lpad * g.q;
+    };
+    int lpv = fp8_lines_per_lane(K);
+    const void *planes_l2 = stage == 1 ? t.fp8_s1_l2 : t.fp8_s2_l2;
+    if (lpv == 4 && planes_l2) {
+        int64_t lp4, lp2;
+        const int64_t b4 = (columns(4, lp4) + 511) / 512, b2 = (columns(2, lp2) + 255) / 256;
+        if ((b2 + nsm - 1) / nsm <= (b4 + nsm - 1) / nsm) lpv = 2;
+    }
+    const int tile = 128 * lpv;
+    const int kslots = lpv > 1 ? 32 : K;
+    ColMapT map;
+    map.stage = stage;
+    map.L = g.L;
+    map.P = g.P;
+    map.n = g.n;
+    map.p = g.p;
+    map.q = g.q;
+    const int64_t ncols = columns(lpv, map.Lpad);
+    const uint8_t *planes = (const uint8_t *)(lpv == 2 && fp8_lines_per_lane(K) == 4
+                                                  ? planes_l2
+                                                  : (stage == 1 ? t.fp8_s1 : t.fp8_s2));
+    const size_t smem = CAR ? fp16_smem_bytes(kslots, 32) : fp8_smem_bytes(kslots, 32);
+    int64_t blocks = (ncols + tile - 1) / tile;
+    if (blocks == 0) return cudaSuccess;
+    if (lpv == 4) {
+        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        stage_fp8_kernel<32, CAR, 4><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, nullptr, map, ncols, K, kslots, in, out, status, nsm);
+    } else if (lpv == 2) {
         err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         stage_fp8_kernel<32, CAR, 2><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(

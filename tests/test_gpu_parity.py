@@ -74,6 +74,35 @@ def test_inverse_and_batch(mode):
     assert bits_equal(y, ref_), mismatch_report(y, ref_)
 
 
+@pytest.mark.parametrize("mode", ["fp8", "fp16"])
+@pytest.mark.parametrize("shape,batch", [((5, 60, 24), 1), ((3, 20, 48), 3), ((1, 240, 12), 1), ((2, 7, 256), 2)])
+def test_two_lines_per_lane_ragged_tiles(mode, shape, batch):
+    """Stages with K <= 16 carry two lines per TMEM lane, 256 lines per CTA,
+    with a block-diagonal constant operand.  Line counts that leave the last
+    tile of a launch (stage 1) or of a twiddle group (stage 2) partly empty,
+    and batches, must stay bit-exact against the oracle."""
+    x = S.complex_uniform(S.SEED_64 + 11, (batch,) + shape if batch > 1 else shape).numpy()
+    pl = plan(shape, mode, batch=batch)
+    sp = splits_of(pl)
+    assert all(max(p, q) <= 16 for p, q in sp if p * q > 1), sp
+    y = run(pl, x)
+    ref_ = oracle_full(x, sp, -1)
+    assert bits_equal(y, ref_), mismatch_report(y, ref_)
+
+
+@pytest.mark.parametrize("mode", ["fp8", "fp16"])
+def test_four_lines_per_lane_sampled(mode):
+    """256 x 256 x 64: the axis-2 stages (K = 8) launch enough CTAs to run
+    four lines per TMEM lane, 512 lines per CTA; the other axes (K = 16) run
+    two.  Every stage of every pass matches the oracle on sampled lines, which
+    land in every slot position of a lane."""
+    shape = (256, 256, 64)
+    pl = plan(shape, mode)
+    assert pl.splits(2) == (8, 8)
+    x = S.complex_uniform(S.SEED_64 + 5, shape, device="cuda")
+    _check_pass_sampled(pl, x, shape, dir=-1, nsample=64)
+
+
 @pytest.mark.parametrize("mode", OZAKI_MODES)
 def test_edge_inputs(mode):
     shape = (8, 8, 16)
