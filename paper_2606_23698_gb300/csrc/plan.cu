@@ -229,7 +229,8 @@ static inline int64_t modc(int64_t x, int64_t m) {
 // INT8 limb table for one stage.  F: [groups][Kout][K][2] int64, K == Kout.
 // Output layout [g][mod][prod][mt][part][kb][lane] uint4 (16 bytes each).
 static std::vector<uint32_t> build_int8_table(const std::vector<int64_t> &F, int groups, int K) {
-    const int KPAD = K <= 32 ? 32 : 64;
+    // K <= 16: the G and H columns share one k32 block (slots 0..15 and 16..31)
+    const int KPAD = K <= 16 ? 16 : (K <= 32 ? 32 : 64);
     const int KB2 = 2 * KPAD / 32;
     const int MT = (K + 15) / 16;
     std::vector<uint32_t> out((size_t)groups * NMOD * 3 * MT * 2 * KB2 * 32 * 4, 0u);

@@ -63,7 +63,11 @@ struct ColMap {
     __device__ __forceinline__ int group(int64_t c) const { return stage == 1 ? 0 : (int)(c / Lpad); }
 };
 
-// smem layout of the data B fragments: [gi 4][mod 12][prod 3][kb KB][limb 2][lane 32] uint2
+// smem layout of the data B fragments: [gi 4][mod 12][prod 3][kb KB][limb 2][lane 32] uint2.
+// KPAD = 16 (K <= 16): the b0 and b1 limbs of the 16 elements share one k32
+// block (k slots 0..15: G b0, 16..31: H b1), so each residue product is one
+// limb GEMM block instead of two half-empty ones: [gi][mod][prod][lane] uint2
+// holding (b0 word, b1 word).
 template <int KPAD, int MT>
 __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__restrict__ table,
                                                               const ModConsts *__restrict__ gmc,
@@ -71,8 +75,10 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
                                                               int Kout,
                                                               const double2 *__restrict__ in,
                                                               double2 *__restrict__ out) {
-    constexpr int KB = KPAD / 32;  // k32 blocks of one limb
-    constexpr int KB2 = 2 * KB;    // limb GEMM blocks (b0 limbs then b1 limbs)
+    constexpr bool PK = KPAD == 16;         // b0 and b1 limbs in one k32 block
+    constexpr int KB = PK ? 1 : KPAD / 32;  // k32 blocks of data elements
+    constexpr int KB2 = PK ? 1 : 2 * KB;    // limb GEMM blocks (b0 limbs then b1 limbs)
+    constexpr int HN = PK ? 1 : 2;          // 16-element halves of a k32 block that hold data
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint2 *sB = reinterpret_cast<uint2 *>(smem_raw);
     __shared__ ModConsts mc;
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
 #pragma unroll
     for (int kb = 0; kb < KB; kb++)
 #pragma unroll
-        for (int h = 0; h < 2; h++)
+        for (int h = 0; h < HN; h++)
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 int j = kb * 32 + h * 16 + 4 * tig + i;
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
     for (int kb = 0; kb < KB; kb++) {
         Pieces pr[2][4], pi[2][4];
 #pragma unroll
-        for (int h = 0; h < 2; h++)
+        for (int h = 0; h < HN; h++)
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 int64_t a = scale_round(xb[kb][h][i][0], e);
@@ -128,9 +134,9 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
         for (int k = sub; k < NMOD; k += MT) {
             const uint32_t m = mc.m[k], mu = mc.barrett[k], c20 = mc.c20[k], c40 = mc.c40[k],
                            cn = mc.c55neg[k];
-            uint32_t w[3][2][2];  // [prod][limb][h]
+            uint32_t w[3][2][2] = {};  // [prod][limb][h]
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
+            for (int h = 0; h < HN; h++) {
                 uint32_t l0[3] = {0, 0, 0}, l1[3] = {0, 0, 0};
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
@@ -152,12 +158,17 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
                 }
             }
 #pragma unroll
-            for (int pd = 0; pd < 3; pd++)
+            for (int pd = 0; pd < 3; pd++) {
+                if constexpr (PK) {
+                    sB[((gi * NMOD + k) * 3 + pd) * 32 + lane] = make_uint2(w[pd][0][0], w[pd][1][0]);
+                } else {
 #pragma unroll
-                for (int limb = 0; limb < 2; limb++) {
-                    int idx = ((((gi * NMOD + k) * 3 + pd) * KB + kb) * 2 + limb) * 32 + lane;
-                    sB[idx] = make_uint2(w[pd][limb][0], w[pd][limb][1]);
+                    for (int limb = 0; limb < 2; limb++) {
+                        int idx = ((((gi * NMOD + k) * 3 + pd) * KB + kb) * 2 + limb) * 32 + lane;
+                        sB[idx] = make_uint2(w[pd][limb][0], w[pd][limb][1]);
+                    }
                 }
+            }
         }
     }
     __syncthreads();
@@ -184,7 +195,8 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
                               (size_t)mt * 2 * KB2 * 32;
 #pragma unroll
             for (int kb = 0; kb < KB2; kb++) {
-                uint2 b = sB[((((gi * NMOD + k) * 3 + pd) * KB + (kb % KB)) * 2 + kb / KB) * 32 + lane];
+                uint2 b = PK ? sB[((gi * NMOD + k) * 3 + pd) * 32 + lane]
+                             : sB[((((gi * NMOD + k) * 3 + pd) * KB + (kb % KB)) * 2 + kb / KB) * 32 + lane];
                 uint4 alo = __ldg(tb + (size_t)(0 * KB2 + kb) * 32 + lane);
                 uint4 ahi = __ldg(tb + (size_t)(1 * KB2 + kb) * 32 + lane);
                 mma_s8(lo, alo, b.x, b.y);
@@ -241,7 +253,7 @@ static cudaError_t launch_t(const AxisTables &t, const ModConsts *dmc, const Col
                             int64_t ncols, int K, int Kout, const double2 *in, double2 *out,
                             cudaStream_t s) {
     const void *table = map.stage == 1 ? t.int8_s1 : t.int8_s2;
-    size_t smem = (size_t)4 * NMOD * 3 * (KPAD / 32) * 2 * 32 * sizeof(uint2);
+    size_t smem = (size_t)4 * NMOD * 3 * (KPAD == 16 ? 1 : (KPAD / 32) * 2) * 32 * sizeof(uint2);
     auto kern = stage_int8_kernel<KPAD, MT>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -266,7 +278,7 @@ cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const S
     int MT = (K + 15) / 16;
     bool wide = K > 32;
     if (!wide) {
-        if (MT == 1) return launch_t<32, 1>(t, dmc, map, ncols, K, K, in, out, s);
+        if (MT == 1) return launch_t<16, 1>(t, dmc, map, ncols, K, K, in, out, s);
         return launch_t<32, 2>(t, dmc, map, ncols, K, K, in, out, s);
     }
     if (MT == 3) return launch_t<64, 3>(t, dmc, map, ncols, K, K, in, out, s);
