@@ -485,9 +485,9 @@ def main():
     fp8_ops = 2 * N3 * (228 * 32 + 32 * 48)
     # DRAM bytes per FP8 stage launch at 1024^3 from one ncu capture of the same
     # kernel on a 16 x 1024 x 1024 grid (256 MiB in and out, above L2):
-    # dram__bytes_read.sum 268,668,928 + dram__bytes_write.sum 222,913,024,
+    # dram__bytes_read.sum 268,671,744 + dram__bytes_write.sum 223,754,752,
     # scaled by the 64 times more columns of a 1024^3 launch
-    traffic = (268668928 + 222913024) * 64 if (mode == "fp8" and n == 1024) else None
+    traffic = (268671744 + 223754752) * 64 if (mode == "fp8" and n == 1024) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinst/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "kernel": f"stage_{mode}_kernel (axis 2, stage 1)", "kernel_ms": kern_ms,

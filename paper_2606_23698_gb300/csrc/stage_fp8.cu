@@ -97,7 +97,7 @@ constexpr int FP8_WARPS = 16;
 // Per-modulus constants (identical for every plan): read through the constant
 // cache, uploaded once per device when the first FP8 plan is created.
 __constant__ ModConsts c_fp8_mc;
-constexpr uint32_t APL_BASE = 320, APL_COLS = 48, N_ABUF = 2;
+constexpr uint32_t APL_BASE = 320, APL_COLS = 48;  // two A buffers
 // FP16 carrier: TMEM columns of one accumulator set (two classes, Re | Im, at
 // npad = 32); the second set follows the first, below the A buffers
 constexpr uint32_t F16_ACC = 128;
@@ -178,35 +178,6 @@ __device__ __forceinline__ void issue_modulus_nm(uint32_t dacc, uint32_t apl, ui
     }
 }
 
-// The same MMAs as issue_modulus_nm, enumerated in that order, split over
-// MMA_ISSUERS threads in different warps (one per SM sub-partition): this
-// thread issues those with index i = part (mod MMA_ISSUERS).  Every MMA
-// accumulates, so every class the modulus touches must hold zero when it
-// starts, and the order in which the issuers' MMAs run does not matter
-// (exact integer sums).
-constexpr int MMA_ISSUERS = 4;
-template <int KIND>
-__device__ __forceinline__ void issue_modulus_part(uint32_t dacc, uint32_t apl, uint64_t bdesc, int npad,
-                                                   int part) {
-    constexpr int ND = KIND == KIND_B11 ? 3 : 2;
-    const uint32_t planeB16 = (uint32_t)npad * 2;
-    const uint32_t cls = 2u * (uint32_t)npad;
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const uint64_t bh = bdesc + (uint64_t)(h * 2 * ND) * planeB16;
-        const uint32_t ah = apl + (uint32_t)(3 * h) * 8;
-        if (KIND == KIND_SQ) {
-            if ((2 * h) % MMA_ISSUERS == part) tc_mma_f8_ta(dacc, ah + 8, bh, instr_desc(128, 4 * npad, 0), 1u);
-            if ((2 * h + 1) % MMA_ISSUERS == part) tc_mma_f8_ta(dacc + cls, ah, bh, instr_desc(128, 2 * npad, 0), 1u);
-        } else {
-#pragma unroll
-            for (int dj = 0; dj < ND; dj++)
-                if ((h * ND + dj) % MMA_ISSUERS == part)
-                    tc_mma_f8_ta(dacc + (uint32_t)dj * cls, ah + (uint32_t)dj * 8, bh,
-                                 instr_desc(128, 2 * ND * npad, 0), 1u);
-        }
-    }
-}
 
 constexpr int fp8_ncls_of_kind(int kind) {
     return kind == KIND_B11 ? 5 : ((kind == KIND_SQ || kind == KIND_F16) ? 2 : 3);
@@ -224,13 +195,12 @@ __device__ __forceinline__ void load_classes(uint32_t tacc, int npad, uint32_t (
             tmem_ld4(tacc + cl * 2 * npad, r[cl]);
     }
 }
-// Zero this thread's columns of the classes the next modulus accumulates into
-// without initialising them: every class of the E4M3 kinds (their MMAs all
-// accumulate, issue_modulus_part); none for the FP16 carrier.
+// Zero this thread's columns of the classes >= 2 (they must start the next
+// modulus at zero, see issue_modulus_nm).
 template <int KIND, int OPT>
 __device__ __forceinline__ void zero_high_classes(uint32_t tacc, int npad) {
 #pragma unroll
-    for (int cl = KIND == KIND_F16 ? 2 : 0; cl < fp8_ncls_of_kind(KIND); cl++) {
+    for (int cl = 2; cl < fp8_ncls_of_kind(KIND); cl++) {
         if constexpr (OPT == 8)
             tmem_st8_const(tacc + cl * 2 * npad, 0u);
         else
@@ -429,10 +399,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     extern __shared__ __align__(1024) uint8_t smem[];
     const ModConsts &mc = c_fp8_mc;
     __shared__ int colpart[4][128];
-    // 0,1: B planes (TMA, per buffer), 2, 3: MMA (FP16 carrier modulus sets;
-    // Phase A), 4: Phase-A B, 5: input tile, 6: E4M3 modulus MMAs (one commit
-    // per issuing thread)
-    __shared__ __align__(8) uint64_t mbar[7];
+    // 0,1: B planes (TMA, per buffer), 2: MMA, 4: Phase-A B, 5: input tile
+    __shared__ __align__(8) uint64_t mbar[6];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
     // FP16 carrier pipeline: failure flags of the steps, read by every thread
@@ -485,7 +453,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             if (CAR) fail[0] = fail[1] = 0;
             s_e0 = itile.e0;
             for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
-            mbar_init(smem_u32(&mbar[6]), MMA_ISSUERS);
             mbar_fence_init();
         }
         __syncwarp();
@@ -511,10 +478,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
-    // E4M3: every class starts at zero (issue_modulus_part accumulates into
-    // all of them); FP16 carrier: not needed (its first MMA initialises)
+    // classes 2..4 start at zero (issue_modulus_nm)
 #pragma unroll
-    for (int cl = CAR ? 5 : 0; cl < 5; cl++)
+    for (int cl = 2; cl < 5; cl++)
 #pragma unroll
         for (int part = 0; part < 2; part++) {
             const uint32_t ta = tmem + lanebase + (uint32_t)(cl * 2 * NPAD + part * NPAD + qd * OPT);
@@ -630,24 +596,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         tma_bulk_g2s(smem_u32(sB0 + (k & 1) * CC::BUF_PLANES * planeB), gplanes + (size_t)CC::plane_offset(k) * planeB,
                      bytes, smem_u32(&mbar[k & 1]));
     };
-    // E4M3: this thread's share of the MMAs of modulus k (part = its warp,
-    // threads 0, 32, 64, 96), committed to mbar[6]
-    auto issue_part = [&](int k, int part) -> bool {
-        if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
-        const uint64_t bd = (k & 1) ? bdesc1 : bdesc0;
-        const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * CC::A_COLS;
-        const int kind = fp8_kind(k);
-        if (kind == KIND_SQ)
-            issue_modulus_part<KIND_SQ>(tmem, apl, bd, NPAD, part);
-        else if (kind == KIND_B9)
-            issue_modulus_part<KIND_B9>(tmem, apl, bd, NPAD, part);
-        else
-            issue_modulus_part<KIND_B11>(tmem, apl, bd, NPAD, part);
-        tc_commit(smem_u32(&mbar[6]));
-        return true;
-    };
-    const bool issuer = !CAR && tid < 32 * MMA_ISSUERS && (tid & 31) == 0;
-    constexpr int PF_TID = CAR ? 32 : 32 * MMA_ISSUERS;  // thread that prefetches constant planes
     auto issue = [&](int k) -> bool {
         if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
         const uint64_t bd = (k & 1) ? bdesc1 : bdesc0;
@@ -669,20 +617,16 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     tmem_wait_st();
     tc_fence_before();
     __syncthreads();
-    if (CAR && tid == 0 && abort_flag == 0) {
+    if (tid == 0 && abort_flag == 0) {
         tc_fence_after();
         if (!issue(0)) abort_flag = 1;
-    } else if (issuer && abort_flag == 0) {
-        tc_fence_after();
-        if (!issue_part(0, tid >> 5)) abort_flag = 1;
-    } else if (tid == PF_TID && NMOD > 1) {
+    } else if (tid == 32 && NMOD > 1) {
         prefetch_b(1);  // buffer 1 is unused so far
     }
     __syncthreads();
     bool ok = abort_flag == 0;
     uint32_t mph[1] = {0u};  // next phase parity of the MMA barrier mbar[2]
     uint32_t mph3 = 0u;      // next phase parity of mbar[3]
-    uint32_t mph6 = 0u;      // next phase parity of mbar[6] (E4M3 modulus MMAs)
     int last_issued = 0, last_waited = -1;  // FP16 carrier, thread 0: MMA batches in flight
     if constexpr (CAR) {
         // FP16 carrier: two accumulator sets.  The MMAs of modulus k+1 (set
@@ -732,8 +676,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         // the next step's barrier.
         for (int k = 0; k < NSTEP && ok; k++) {
             if (k + 1 < NMOD) gen(k + 1);  // digits of the next modulus while this one's MMAs run
-            const bool okm = mbar_wait(smem_u32(&mbar[6]), mph6, WAIT_LIMIT);
-            mph6 ^= 1u;
+            const bool okm = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+            mph[0] ^= 1u;
             tc_fence_after();
             if (okm) {
                 const uint32_t tre = tmem + lanebase + (uint32_t)(qd * OPT);
@@ -754,14 +698,13 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 ok = false;
                 break;
             }
-            // MMAs of modulus k+1 from the four issuing threads; the constant
-            // planes of modulus k+2 from another warp, into the buffer of
-            // modulus k (its MMAs completed: every thread waited for them
-            // before this barrier)
-            if (issuer && k + 1 < NSTEP) {
+            // MMAs of modulus k+1 from thread 0; the constant planes of modulus k+2
+            // from another warp, into the buffer of modulus k (its MMAs completed:
+            // every thread waited for them before this barrier)
+            if (tid == 0 && k + 1 < NSTEP) {
                 tc_fence_after();
-                if (!issue_part(k + 1, tid >> 5)) abort_flag = 1;
-            } else if (tid == PF_TID && k + 2 < NSTEP) {
+                if (!issue(k + 1)) abort_flag = 1;
+            } else if (tid == 32 && k + 2 < NSTEP) {
                 prefetch_b(k + 2);
             }
         }
@@ -895,7 +838,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             for (int j = last_waited + 1; j <= last_issued; j++)
                 mbar_wait(smem_u32(&mbar[2 + (j & 1)]), (uint32_t)((j >> 1) & 1), WAIT_LIMIT);
         }
-        if (!CAR) mbar_wait(smem_u32(&mbar[6]), mph6, WAIT_LIMIT);
         mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
         if (pend3) mbar_wait(smem_u32(&mbar[3]), mph3, WAIT_LIMIT);
         mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
