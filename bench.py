@@ -14,6 +14,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import statistics
 import os
 import subprocess
 import sys
@@ -32,7 +33,7 @@ SHAPE = (1024, 1024, 1024)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default=None, help="fp8 | int8 | fp16 (headline Ozaki mode)")
@@ -364,25 +365,29 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def time_mode(m, steps, warmup):
+    def time_mode(m, steps, warmup, per_step=None):
         pl = Plan(*shape, mode=m)
         for _ in range(warmup):
             pl.exec(x, y)
         barrier()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for i in range(steps):
             pl.exec(x, y)
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         barrier()
-        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device="cuda")
+        ms = max_over_ranks(dist, evs[0].elapsed_time(evs[-1]), device="cuda")
+        if per_step is not None:  # the individual step times, for the median
+            per_step.extend(evs[i].elapsed_time(evs[i + 1]) for i in range(steps))
         return pl, ms
 
     # headline mode, timed with clock sampling
+    step_ms = []
     with ClockSampler(local) as clk:
-        pl, ms_total = time_mode(mode, args.steps, args.warmup)
+        pl, ms_total = time_mode(mode, args.steps, args.warmup, step_ms)
     clocks = clk.summary()
     ms_step = ms_total / args.steps
+    ms_step_median = float(statistics.median(step_ms)) if step_ms else ms_step
     y_main = y.clone()
 
     # dominant kernel: one stage launch (axis 2, stage 1), timed alone with events
@@ -506,7 +511,8 @@ def main():
                "fp64_fft_oracle": {"value": fms, "unit": "ms", "cores": fcores, "sample": fsample}}
     launches = 6 * args.steps  # six stage kernels per 3-D transform
     line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+            "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_step_median": ms_step_median,
+            "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp8": "e4m3", "int8": "s8", "fp16": "f16", "fp64": "f64"}[mode],
             "data": "synthetic",
