@@ -156,6 +156,33 @@ def test_full_size_1024cube_sampled_and_parseval(mode):
     torch.cuda.empty_cache()
 
 
+def test_full_size_1024cube_all_modes_bit_identical():
+    """The three Ozaki modes compute the same exact integer pipeline, so at
+    1024^3 their 2^30 outputs must agree bit for bit.  This checks every
+    output of the benchmark workload (not a sample), and three different
+    kernels would not share a wrong value."""
+    shape = (1024, 1024, 1024)
+    if torch.cuda.get_device_properties(0).total_memory < 120 * 2 ** 30:
+        pytest.skip("needs ~100 GiB of device memory")
+    x = S.complex_uniform(S.SEED_1024, shape, device="cuda")
+    ref_y = None
+    for mode in ("fp8", "fp16", "int8"):
+        pl = plan(shape, mode)
+        y = pl.exec(x, dir=-1)
+        torch.cuda.synchronize()
+        pl.close()
+        if ref_y is None:
+            ref_y = y
+            continue
+        same = torch.equal(y.view(torch.int64), ref_y.view(torch.int64))
+        ndiff = 0 if same else int((y.view(torch.int64) != ref_y.view(torch.int64)).sum())
+        del y
+        torch.cuda.empty_cache()
+        assert same, f"{mode}: {ndiff} of {2 * 1024 ** 3} doubles differ from fp8"
+    del x, ref_y
+    torch.cuda.empty_cache()
+
+
 # 16 sampled outputs: DC, the Nyquist corner, axis-aligned and seeded random frequencies
 SPOTS_1024 = [(0, 0, 0), (1, 2, 3), (511, 17, 1000), (1023, 1023, 1023), (512, 512, 512), (5, 700, 300),
               (0, 0, 1), (0, 1023, 0), (1, 0, 0)] + \
