@@ -46,7 +46,7 @@ def test_gradient_matches_oracle_and_finite_differences(mode):
         yy = fft3_autograd(v.reshape(x0.shape).to("cuda"), mode)
         return float((torch.abs(yy * wd) ** 2).sum())
 
-    for idx in rng.choice(flat.numel(), size=8, replace=False):
+    for idx in rng.choice(flat.numel(), size=16, replace=False):  # 32 real coordinates
         for part in (1.0, 1j):
             xp = flat.clone()
             xm = flat.clone()
