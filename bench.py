@@ -287,10 +287,23 @@ def side_configs(torch, Plan, PlanMany, S, mode):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / 3
+    # per-size error: the same grids through the native FP64 kernels
+    outs64 = [torch.empty_like(t) for t in xs]
+    pm64 = PlanMany(dims, mode="fp64")
+    pm64.exec(xs, outs64)
+    torch.cuda.synchronize()
+    per_size = {}
+    for d, o, r in zip(dims, outs, outs64):
+        key = "x".join(str(v) for v in d)
+        e = float(torch.linalg.vector_norm(o - r) / torch.linalg.vector_norm(r))
+        per_size[key] = max(per_size.get(key, 0.0), e)
+    pm64.close()
+    del outs64
     out["uneven_batch_40_grids"] = {"mode": mode, "ms": ms, "grids_per_s": len(dims) / (ms * 1e-3),
                                     "elements": int(sum(d[0] * d[1] * d[2] for d in dims)),
                                     "execution": "one CUDA graph launch per call; grids of one shape batched",
-                                    "splits": "autotuned"}
+                                    "splits": "autotuned",
+                                    "max_rel_diff_vs_fp64_per_size": per_size}
     pm.close()
     del xs, outs
     # differentiable transform: 8 x 128^3, loss = sum |F(x) w|^2, forward + backward
