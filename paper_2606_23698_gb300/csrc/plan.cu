@@ -544,10 +544,10 @@ static obfft_status build_tables(obfft_plan P, AxisTables &t) {
     } else if (P->mode == OBFFT_MODE_FP32) {
         e = fp32_upload_constants();
         if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("FP32 constants: ") + cudaGetErrorString(e));
-        std::vector<uint8_t> s1 = build_fp16_planes(t.Fq, 1, t.q, kModuli32, NMOD32);
-        std::vector<uint8_t> s2 = build_fp16_planes(t.Fp, t.q, t.p, kModuli32, NMOD32);
-        e = upload(s1.data(), s1.size(), &t.fp8_s1);
-        if (e == cudaSuccess) e = upload(s2.data(), s2.size(), &t.fp8_s2);
+        e = upload_planes(t, [&](const std::vector<int64_t> &F, int groups, int K, int lpv) {
+            return lpv > 1 ? build_fp16_planes(lane_blocks(F, groups, K, lpv), groups, 32, kModuli32, NMOD32)
+                           : build_fp16_planes(F, groups, K, kModuli32, NMOD32);
+        });
     } else if (P->mode == OBFFT_MODE_FP32_NATIVE) {
         std::vector<float> tw;
         auto push = [&](int N) {

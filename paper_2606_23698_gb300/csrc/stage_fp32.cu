@@ -120,17 +120,17 @@ __device__ __forceinline__ uint32_t stage32_off(uint32_t row, uint32_t k) {
     return (row >> 3) * PA32_ROWB + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// Input tile of the columns [cb, cb + 128) (element = 8 bytes): stage 1 one
+// Input tile of the columns [cb, cb + width) (element = 8 bytes): stage 1 one
 // contiguous element range [e0, e1), stage 2 K elements per column at
 // src0 + i n.  In shared memory stage-2 column i starts at i (K + 2) elements.
 struct InputTile32 {
     int64_t e0, e1, src0, n;
     int nvalid;
 };
-__device__ __forceinline__ InputTile32 input_tile32(const ColMapT &map, int64_t ncols, int64_t cb) {
+__device__ __forceinline__ InputTile32 input_tile32(const ColMapT &map, int64_t ncols, int64_t cb, int width) {
     InputTile32 t;
     if (map.stage == 1) {
-        const int64_t l0 = cb / map.p, l1 = min(cb + 127, ncols - 1) / map.p;
+        const int64_t l0 = cb / map.p, l1 = min(cb + width - 1, ncols - 1) / map.p;
         t.e0 = l0 * map.n;
         t.e1 = (l1 + 1) * map.n;
         t.src0 = 0;
@@ -141,7 +141,7 @@ __device__ __forceinline__ InputTile32 input_tile32(const ColMapT &map, int64_t 
         t.e0 = t.e1 = 0;
         t.src0 = l0 * map.n + k2 * map.p;
         t.n = map.n;
-        t.nvalid = (int)max((int64_t)0, min((int64_t)128, map.L - l0));
+        t.nvalid = (int)max((int64_t)0, min((int64_t)width, map.L - l0));
     }
     return t;
 }
@@ -201,8 +201,12 @@ __device__ __forceinline__ void prefetch_input_tile32(const ColMapT &map, const 
 // of modulus k+1 run while the epilogue of modulus k reads its set; FP16 A
 // buffers of the data residues at 8 npad + b npad (x_R in the first npad / 2
 // columns, x_I in the next); Phase A reuses [0, 8 x 32).
+// LPV = 2 or 4 (K <= 16 or K <= 8, NPAD = 32): LPV lines per TMEM lane, as
+// in the FP8 / FP16-carrier stage kernel: line h in slots [KS h, KS h + KS)
+// with block-diagonal constants; quarter-warp group qd works on line
+// qd / (4 / LPV) only; a CTA covers 128 LPV lines.
 // ---------------------------------------------------------------------------
-template <int NPAD>
+template <int NPAD, int LPV>
 __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     stage_fp32_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab, ColMapT map,
                       int64_t ncols, int K, int Kout, const float2 *__restrict__ in, float2 *__restrict__ out,
@@ -219,12 +223,17 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     __shared__ __align__(8) uint64_t mbar[7];
     __shared__ uint32_t tmem_holder;
 
+    static_assert(LPV == 1 || (NPAD == 32 && (LPV == 2 || LPV == 4)), "1, 2 or 4 lines per lane");
+    constexpr int QPL = 4 / LPV;      // quarter-warp groups per line
+    constexpr int TILE = 128 * LPV;   // columns (lines) per CTA
+    constexpr int KS = NPAD / LPV;    // slots of one line
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int sub = w & 3, qd = w >> 2;
     const int c = 32 * sub + lane;
+    const int hl = qd / QPL;  // this thread's line within its lane
     const uint32_t lanebase = (uint32_t)(32 * sub) << 16;
-    const int64_t cbase = (int64_t)blockIdx.x * 128;
-    const int64_t cg = cbase + c;
+    const int64_t cbase = (int64_t)blockIdx.x * TILE;
+    const int64_t cg = cbase + 128 * hl + c;
     const bool cvalid = map.valid(cg, ncols);
     const int group = map.group(cbase);
 
@@ -239,7 +248,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     if (w == 0) {
         tmem_alloc(smem_u32(&tmem_holder), 512);
     } else if (w == 1) {
-        const InputTile32 itile = input_tile32(map, ncols, cbase);
+        const InputTile32 itile = input_tile32(map, ncols, cbase, TILE);
         if (lane == 0) {
             s_e0 = itile.e0;
             for (int b = 0; b < 7; b++) mbar_init(smem_u32(&mbar[b]), 1);
@@ -256,14 +265,14 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     } else if (w == 2) {
         const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
         if (tma_in && pf_ahead > 0 && nb < (int64_t)gridDim.x)
-            prefetch_input_tile32(map, input_tile32(map, ncols, nb * 128), K, in, lane);
+            prefetch_input_tile32(map, input_tile32(map, ncols, nb * TILE, TILE), K, in, lane);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
     if (!tma_in) {
-        load_input_tile32(map, input_tile32(map, ncols, cbase), K, in, sIn, tid);
+        load_input_tile32(map, input_tile32(map, ncols, cbase, TILE), K, in, sIn, tid);
         __syncthreads();
     }
 
@@ -276,20 +285,22 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     {
         const bool okin = tma_in ? mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT32) : true;
         if (!okin) bad = true;
-        const int64_t sbase = map.stage == 1 ? ibase - s_e0 : (int64_t)c * (K + 2);
+        const int64_t sbase = map.stage == 1 ? ibase - s_e0 : (int64_t)(128 * hl + c) * (K + 2);
         const int64_t sstride = map.stage == 1 ? istride : 1;
         float2 x[EPT];
         int lead = LEAD_ZERO;
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) {
-            const int j = EPT * qd + jj;
+            const int j = EPT * qd + jj - KS * hl;
             x[jj] = make_float2(0.f, 0.f);
             if (okin && cvalid && j < K) x[jj] = *reinterpret_cast<const float2 *>(sIn + (sbase + (int64_t)j * sstride) * 8);
             lead = max(lead, max(lead_exponent32(__float_as_uint(x[jj].x)), lead_exponent32(__float_as_uint(x[jj].y))));
         }
         colpart[qd][c] = lead;
         __syncthreads();
-        const int l2 = max(max(colpart[0][c], colpart[1][c]), max(colpart[2][c], colpart[3][c]));
+        int l2 = colpart[QPL * hl][c];
+#pragma unroll
+        for (int i = 1; i < QPL; i++) l2 = max(l2, colpart[QPL * hl + i][c]);
         e = l2 == LEAD_ZERO ? 0 : l2;
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) xt[jj] = scale_round2(x[jj], e);
@@ -444,15 +455,23 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         const uint64_t bdescA = smem_desc(smem_u32(sPAB), 128, 256);
         const uint64_t M = mc.M;
         const int64_t halfM = mc.halfM;
+        // output slot of row block bi of the wave starting at b0 (with LPV
+        // lines per lane, the thread finishing blocks qd and qd + 4 stays on
+        // its own line; see the FP8 stage kernel)
+        auto kout_of = [&](int b0, int bi) -> int {
+            if constexpr (LPV == 1) return b0 + bi;
+            else if constexpr (LPV == 2) return KS * ((bi & 3) >> 1) + (b0 >> 1) + 2 * (bi >> 2) + (bi & 1);
+            else return KS * (bi & 3) + (b0 >> 2) + (bi >> 2);
+        };
         for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
             const int nb = min(per_wave, Kout - b0);
             const int nb_next = min(per_wave, Kout - b0 - per_wave);
             if (tid == 0) {
                 tc_fence_after();
-                uint64_t ad = adescA + (uint64_t)((uint32_t)b0 * (16 * PA32_ROWB / 16));
                 for (int bi = 0; bi < nb; bi++) {
+                    // a row block is 16 row groups: 16 x PA32_ROWB bytes per output slot
+                    const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b0, bi) * (16 * PA32_ROWB / 16));
                     tc_mma_f16(tmem + (uint32_t)(bi * PA32_N), ad, bdescA, idescA, 1);
-                    ad += 16 * PA32_ROWB / 16;  // next row block: 16 row groups
                 }
                 tc_commit(smem_u32(&mbar[6]));
                 pendA = true;
@@ -488,8 +507,8 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
                     if (bi < nb_next) preset(bi);
                     const float re = crt_pack32(wr, e - 46, M, halfM);
                     const float im = crt_pack32(wi, e - 46, M, halfM);
-                    const int kout = b0 + bi;
-                    if (cvalid) out[obase + (int64_t)kout * ostride] = make_float2(re, im);
+                    const int kl = kout_of(b0, bi) - KS * hl;  // output index within this thread's line
+                    if (cvalid && kl < K) out[obase + (int64_t)kl * ostride] = make_float2(re, im);
                 }
             }
             tmem_wait_st();
@@ -532,40 +551,60 @@ size_t fp32_smem_bytes(int Kout, int npad) {
 
 cudaError_t launch_stage_fp32(const AxisTables &t, const void *pab, int *status, const StageGeom &g, int stage,
                               const float2 *in, float2 *out, cudaStream_t s) {
-    ColMapT map;
-    map.stage = stage;
-    map.L = g.L;
-    map.Lpad = (g.L + 127) / 128 * 128;
-    map.P = g.P;
-    map.n = g.n;
-    map.p = g.p;
-    map.q = g.q;
     const int K = stage == 1 ? g.q : g.p;
     if (K > 32) return cudaErrorInvalidValue;
-    const int npad = K <= 16 ? 16 : 32;
-    const int64_t ncols = stage == 1 ? g.L * g.p : map.Lpad * g.q;
-    const uint8_t *planes = (const uint8_t *)(stage == 1 ? t.fp8_s1 : t.fp8_s2);
-    const size_t smem = fp32_smem_bytes(K, npad);
-    const int64_t blocks = (ncols + 127) / 128;
-    if (blocks == 0) return cudaSuccess;
-    // TMA bulk copies of the input need 16-byte aligned starts and sizes: an
-    // even line length (stage 1), even n and K (stage 2), aligned base
-    const int tma_in = ((uintptr_t)in % 16 == 0) && (g.n % 2 == 0) && (stage == 1 || K % 2 == 0);
     int dev = 0, nsm = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    if (npad == 16) {
-        err = cudaFuncSetAttribute(stage_fp32_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // lines per TMEM lane, chosen as in the FP8 / FP16-carrier launcher: four
+    // (K <= 8) only when they need fewer rounds of CTAs than two
+    auto columns = [&](int lpv, int64_t &Lpad) {
+        const int64_t tile = 128 * lpv;
+        Lpad = (g.L + tile - 1) / tile * tile;
+        return stage == 1 ? g.L * g.p : Lpad * g.q;
+    };
+    int lpv = fp8_lines_per_lane(K);
+    const void *planes_l2 = stage == 1 ? t.fp8_s1_l2 : t.fp8_s2_l2;
+    if (lpv == 4 && planes_l2) {
+        int64_t lp4, lp2;
+        const int64_t b4 = (columns(4, lp4) + 511) / 512, b2 = (columns(2, lp2) + 255) / 256;
+        if ((b2 + nsm - 1) / nsm <= (b4 + nsm - 1) / nsm) lpv = 2;
+    }
+    const int tile = 128 * lpv, kslots = lpv > 1 ? 32 : K;
+    ColMapT map;
+    map.stage = stage;
+    map.L = g.L;
+    map.P = g.P;
+    map.n = g.n;
+    map.p = g.p;
+    map.q = g.q;
+    const int64_t ncols = columns(lpv, map.Lpad);
+    const uint8_t *planes = (const uint8_t *)(lpv == 2 && fp8_lines_per_lane(K) == 4
+                                                  ? planes_l2
+                                                  : (stage == 1 ? t.fp8_s1 : t.fp8_s2));
+    const size_t smem = fp32_smem_bytes(kslots, 32);
+    const int64_t blocks = (ncols + tile - 1) / tile;
+    if (blocks == 0) return cudaSuccess;
+    // TMA bulk copies of the input need 16-byte aligned starts and sizes: an
+    // even line length (stage 1), even n and K (stage 2), aligned base
+    const int tma_in = ((uintptr_t)in % 16 == 0) && (g.n % 2 == 0) && (stage == 1 || K % 2 == 0);
+    if (lpv == 4) {
+        err = cudaFuncSetAttribute(stage_fp32_kernel<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp32_kernel<16><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, map, ncols, K, K, in, out, status, nsm, tma_in);
+        stage_fp32_kernel<32, 4><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, map, ncols, K, kslots, in, out, status, nsm, tma_in);
+    } else if (lpv == 2) {
+        err = cudaFuncSetAttribute(stage_fp32_kernel<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        stage_fp32_kernel<32, 2><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, map, ncols, K, kslots, in, out, status, nsm, tma_in);
     } else {
-        err = cudaFuncSetAttribute(stage_fp32_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(stage_fp32_kernel<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        stage_fp32_kernel<32><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, map, ncols, K, K, in, out, status, nsm, tma_in);
+        stage_fp32_kernel<32, 1><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
+            planes, (const uint8_t *)pab, map, ncols, K, kslots, in, out, status, nsm, tma_in);
     }
     return cudaGetLastError();
 }

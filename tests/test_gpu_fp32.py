@@ -122,6 +122,28 @@ def test_fp32_wide_range_256_stage_sampled():
     _check_pass_sampled(pl, x, shape, dir=-1, nsample=48)
 
 
+def test_fp32_four_lines_per_lane_sampled():
+    """256 x 256 x 64: the axis-2 stages (K = 8) run four lines per TMEM
+    lane, the others (K = 16) two; sampled lines of every stage match the
+    oracle bit for bit."""
+    shape = (256, 256, 64)
+    pl = plan(shape)
+    assert pl.splits(2) == (8, 8)
+    x = S.complex_uniform(S.SEED_64 + 5, shape, device="cuda").to(torch.complex64)
+    _check_pass_sampled(pl, x, shape, dir=-1, nsample=64)
+
+
+@pytest.mark.parametrize("shape,batch", [((5, 60, 24), 1), ((3, 20, 48), 3), ((1, 240, 12), 1)])
+def test_fp32_lines_per_lane_ragged_tiles(shape, batch):
+    """Line counts that leave the last tile of a launch or of a twiddle group
+    partly empty, with two lines per lane, stay bit-exact."""
+    x = S.complex_uniform(S.SEED_64 + 11, (batch,) + shape if batch > 1 else shape).numpy()
+    pl = plan(shape, batch=batch)
+    y = run(pl, x)
+    ref_ = oracle32(c64(x), splits_of(pl), -1)
+    assert same_bits(y, ref_), report(y, ref_)
+
+
 def test_fp32_full_size_1024cube_sampled_and_parseval():
     """1024^3 complex64 (8 GiB), splits 32 x 32: every stage of every axis pass
     matches the oracle on sampled lines; the transform satisfies Parseval."""
