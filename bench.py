@@ -224,7 +224,7 @@ def fp32_variant(torch, Plan, x, y64, stream):
                 # one ncu capture of the same kernel on 16 x 1024 x 1024 complex64
                 # (128 MiB in and out): dram read 134,478,592 + write 91,217,152 bytes,
                 # scaled by the 64 times more columns of a 1024^3 launch
-                "traffic": (134478592 + 91217152) * 64 if N3 == 1024 ** 3 else None}
+                "traffic": (134427136 + 89783808) * 64 if N3 == 1024 ** 3 else None}
             del scratch
         out[m] = res
         pl.close()
