@@ -1031,11 +1031,12 @@ extern "C" obfft_status obfft_exec_host(obfft_plan p, const void *host_in, void 
         }
     char *d0 = (char *)p->host_io[0], *d1 = (char *)p->host_io[1];
     char *scr = (char *)p->scratch;
-    // chunks: up to 16 per batch item, never fewer than 2^20 elements each
+    // chunks: up to 64 per batch item (smaller chunks shorten the exposed
+    // first copy and last copy-back), never fewer than 2^20 elements each
     const int64_t n2 = gd.ax[2].n, n0 = gd.ax[0].n;
     const int64_t P2 = gd.n[0] * gd.n[1], P0 = gd.n[1] * gd.n[2];
     auto nchunks = [](int64_t lines, int64_t len) {
-        int64_t c = std::min<int64_t>(16, std::max<int64_t>(1, lines * len / ((int64_t)1 << 20)));
+        int64_t c = std::min<int64_t>(64, std::max<int64_t>(1, lines * len / ((int64_t)1 << 20)));
         return (int)std::min<int64_t>(c, lines);
     };
     const int c2 = nchunks(P2, n2), c0 = nchunks(P0, n0);
