@@ -301,3 +301,29 @@ def test_fp32_stage_entry_matches_oracle_stage():
     r1 = r1.reshape(-1, p, q).transpose(0, 2, 1).reshape(-1, N)
     got = out.reshape(L, N).cpu().numpy()
     assert same_bits(got, r1), report(got, r1)
+
+
+def _random_cases(n_cases=48, seed=20261204):
+    lengths = [1, 2, 3, 5, 7, 8, 11, 12, 16, 17, 20, 24, 27, 31, 32, 36, 40, 48, 60, 64, 96, 100, 128, 256]
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n_cases:
+        shape = tuple(int(rng.choice(lengths)) for _ in range(3))
+        elems = shape[0] * shape[1] * shape[2]
+        if elems > 80000 or elems < 8:
+            continue
+        batch = int(rng.integers(1, 4)) if elems < 15000 else 1
+        out.append((shape, batch, -1 if rng.random() < 0.7 else +1))
+    return out
+
+
+@pytest.mark.parametrize("shape,batch,dirn", _random_cases())
+def test_fp32_random_shape_bit_exact(shape, batch, dirn):
+    """Seeded random shapes, batches and directions (one, two and four lines
+    per TMEM lane, prime lengths): bit-exact against the oracle."""
+    full = (batch,) + shape if batch > 1 else shape
+    x = S.complex_gaussian(S.SEED_64 + sum(shape) + batch, full).numpy()
+    pl = plan(shape, batch=batch)
+    y = run(pl, x, dir=dirn)
+    ref_ = oracle32(c64(x), splits_of(pl), dirn)
+    assert same_bits(y, ref_), report(y, ref_)
