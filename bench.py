@@ -25,7 +25,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "1024^3 Z2Z 3-D FFT ms & % roofline: Ozaki FP8/INT8 vs native FP64, err≤1e-14"
-# mma.sync m16n8k32 s8 rate measured on this GPU by probes/simt_int8_peak.cu
+# mma.sync m16n8k32 s8 rate measured on this GPU by a stand-alone probe kernel
+# (152 CTAs x 16 warps, four independent m16n8k32 s8 chains per warp)
 INT8_MMA_SYNC_TOPS = 150.9
 SHAPE = (1024, 1024, 1024)
 
@@ -41,6 +42,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the side configurations")
+    ap.add_argument("--case", nargs="+", default=None,
+                    help="run one small GPU invocation for a profiler capture instead of the benchmark: "
+                         "'stage D0 D1 D2 AXIS STAGE MODE' | 'fft3 D0 D1 D2 MODE' | 'ablation'")
     return ap.parse_args()
 
 
@@ -332,6 +336,53 @@ def side_configs(torch, Plan, PlanMany, S, mode):
     return out
 
 
+def run_case(argv):
+    """One small, self-contained GPU invocation for profiler captures (prints one
+    line, exits 0): `stage` runs a single stage launch (Bailey stage 1 or 2 of one
+    axis pass) of a D0 x D1 x D2 plan on seeded uniform input; `fft3` runs one
+    forward transform; `ablation` runs each epilogue ablation kernel once (four
+    Phase-B word layouts, three residue forms; 2^22 items from 2^16 L2-resident
+    inputs, 16 perturbed repetitions each)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_23698_gb300 import Plan, _lib
+    from synth import inputs as S
+    what = argv[0]
+    if what == "ablation":
+        import numpy as np
+        from paper_2606_23698_gb300.ablation import PHASE_B_VARIANTS, RESIDUE_VARIANTS, phase_b_inputs, \
+            residue_inputs
+        nu, nt = 1 << 16, 1 << 22
+        acc, et = phase_b_inputs(nu)
+        dacc, det = torch.from_numpy(acc.view(np.int32)).cuda(), torch.from_numpy(et).cuda()
+        ck = torch.zeros(1, dtype=torch.int64, device="cuda")
+        for v in PHASE_B_VARIANTS:
+            _lib.obfft_ablation_phase_b(v, nu, nt, dacc.data_ptr(), det.data_ptr(), None, ck.data_ptr(), reps=16)
+        xt = torch.from_numpy(residue_inputs(nu)).cuda()
+        for v in RESIDUE_VARIANTS:
+            _lib.obfft_ablation_residues(v, nu, nt, xt.data_ptr(), None, ck.data_ptr(), reps=16)
+        torch.cuda.synchronize()
+        print("ok ablation", int(ck.item()))
+        return
+    shape = tuple(int(v) for v in argv[1:4])
+    if what == "stage":
+        axis, stage, mode = int(argv[4]), int(argv[5]), argv[6]
+        pl = Plan(*shape, mode=mode)
+        x = S.complex_uniform(1, shape, device="cuda").to(pl.dtype)
+        out = torch.empty_like(x)
+        pl.exec_stage(axis, stage, x, out)
+    elif what == "fft3":
+        pl = Plan(*shape, mode=argv[4])
+        x = S.complex_uniform(1, shape, device="cuda").to(pl.dtype)
+        out = torch.empty_like(x)
+        pl.exec(x, out)
+    else:
+        raise SystemExit(f"unknown case {what!r}")
+    torch.cuda.synchronize()
+    print("ok", what, shape, float(out.abs().sum()))
+
+
 def max_over_ranks(dist, value: float, device="cpu") -> float:
     """Whole-job time of N replicas: the slowest rank's time (all_reduce MAX)."""
     if dist is None:
@@ -345,6 +396,9 @@ def max_over_ranks(dist, value: float, device="cpu") -> float:
 # --------------------------------------------------------------- our arm ----
 def main():
     args = parse()
+    if args.case:
+        run_case(args.case)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
