@@ -118,7 +118,9 @@ obfft_status obfft_plan_create_many(obfft_plan *out, int count, const int64_t *d
 
 /*
  * Transform every grid of a _many plan: ins[g] / outs[g] are device pointers
- * (arrays of `count` pointers in HOST memory).  Asynchronous on `stream`.
+ * (arrays of `count` pointers in HOST memory).  Every output range must be
+ * disjoint from every input range and from every other output range (inputs
+ * may share memory); OBFFT_ERR_ARG otherwise.  Asynchronous on `stream`.
  * The work (per group: device-to-device gathers of the members, six batched
  * stage launches, scatters of the results) is captured once into a CUDA
  * graph per set of pointers and direction, and replayed by later calls.  The
@@ -257,7 +259,8 @@ obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_to
  * or applications that hand a library only the buffers it works on).
  *
  * It runs the native-FP64 six-step path (the kernels of OBFFT_MODE_FP64_NATIVE
- * plans, bit-identical results) on one n0 x n1 x n2 grid, with the stage-to-
+ * plans with their default Bailey splits, so results are bit-identical to a
+ * plan created without OBFFT_AUTOTUNE=1) on one n0 x n1 x n2 grid, with the stage-to-
  * stage scratch and the twiddle tables in device memory that the library
  * reserves at load time (file-scope device arrays, about 32 MiB per GPU that
  * loads the library, held until the process exits).  in/out: device pointers
@@ -271,14 +274,19 @@ obfft_status obfft_ablation_residues(int variant, int64_t n_unique, int64_t n_to
  *    on a device looks up the device addresses of the reserved arrays
  *    (cudaGetSymbolAddress, with that device current); with the CUDA driver's
  *    lazy module loading this first call is also when the driver places the
- *    arrays in device memory.  Make that first call during set-up, before any
- *    stream capture; later calls leave free device memory unchanged.
+ *    arrays in device memory.  Make that first call during set-up; later calls
+ *    leave free device memory unchanged.  The addresses are kept per device
+ *    and CUDA context: after cudaDeviceReset the next call looks them up again.
+ *  - Not for stream capture: every call uploads the twiddles of its three
+ *    axes from a static pageable host table (a copy a captured graph could not
+ *    replay with the right contents).
  *  - Every call on a device shares the same reserved arrays, which keep the
  *    last call's contents.  Nothing in them needs to start at zero (the scratch
  *    is fully written before it is read, the twiddles are rewritten by every
  *    call).  Calls whose work overlaps on the GPU (e.g. on two streams) race
  *    on these arrays and give wrong results: serialise them.
- *  - The twiddle upload is a host-to-device copy from pageable memory.
+ *  - The twiddle upload is a host-to-device copy from pageable memory of
+ *    the n + p + q entries each transformed axis uses.
  */
 obfft_status obfft_exec_fp64_noalloc(const void *in, void *out, int64_t n0, int64_t n1, int64_t n2, int dir,
                                      void *stream);

@@ -109,6 +109,10 @@ struct GridDesc {
     AxisPlan ax[3];
 };
 
+// Default Bailey split of an axis of length n: q = smallest divisor with
+// q^2 >= n, p = n / q, both <= kmax; false when n does not factor that way.
+bool choose_split(int64_t n, AxisPlan *a, int kmax = KMAX);
+
 }  // namespace obfft
 
 struct obfft_plan_s {

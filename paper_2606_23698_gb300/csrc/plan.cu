@@ -599,16 +599,19 @@ AxisTables *get_tables(obfft_plan P, int n, int pp, int qq, int dir) {
     return nullptr;
 }
 
-// Bailey split: q = smallest divisor >= sqrt(n), p = n / q; both <= 64.
-static bool choose_split(int64_t n, AxisPlan *a, int kmax = KMAX) {
+// Bailey split: q = smallest divisor >= sqrt(n), p = n / q; both <= kmax.
+// Lengths above kmax^2 cannot factor within the limit and are rejected before
+// the search, which then visits at most kmax candidates.
+bool choose_split(int64_t n, AxisPlan *a, int kmax) {
+    if (n < 1 || n > (int64_t)kmax * kmax) return false;
     if (n == 1) {
         a->n = 1; a->p = 1; a->q = 1;
         return true;
     }
-    for (int64_t q = 1; q <= n; q++)
+    for (int64_t q = 1; q <= kmax; q++)
         if (n % q == 0 && q * q >= n) {
-            int64_t p = n / q;
-            if (p > kmax || q > kmax) return false;
+            const int64_t p = n / q;
+            if (p > kmax) return false;
             a->n = (int)n; a->p = (int)p; a->q = (int)q;
             return true;
         }
@@ -1147,6 +1150,29 @@ extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, vo
     for (size_t g = 0; g < G; g++) {
         obfft_status st = check_ptrs(ins[g], outs[g]);
         if (st != OBFFT_OK) return st;
+    }
+    // the groups run as concurrent graph branches: no output may overlap any
+    // input or any other output (inputs are only read and may share memory)
+    {
+        const size_t eb = elem_bytes(p->mode);
+        std::vector<size_t> bytes(G);
+        for (size_t g = 0; g < G; g++) {
+            const GridDesc &gd = p->grids[g];
+            bytes[g] = (size_t)(gd.n[0] * gd.n[1] * gd.n[2]) * (G == 1 ? (size_t)p->batch : 1) * eb;
+        }
+        auto overlap = [](const void *a, size_t na, const void *b, size_t nb) {
+            const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+            return x < y + nb && y < x + na;
+        };
+        for (size_t h = 0; h < G; h++)
+            for (size_t g = 0; g < G; g++) {
+                if (overlap(outs[h], bytes[h], ins[g], bytes[g]))
+                    return set_error(OBFFT_ERR_ARG, "output " + std::to_string(h) + " overlaps input " +
+                                                        std::to_string(g));
+                if (g != h && overlap(outs[h], bytes[h], outs[g], bytes[g]))
+                    return set_error(OBFFT_ERR_ARG, "outputs " + std::to_string(h) + " and " + std::to_string(g) +
+                                                        " overlap");
+            }
     }
     cudaStream_t s = (cudaStream_t)stream;
     bool same = p->graph_exec && p->graph_dir == dir && p->graph_ins.size() == G;

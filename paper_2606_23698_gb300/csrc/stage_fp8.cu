@@ -402,7 +402,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // 0,1: B planes (TMA, per buffer), 2: MMA, 4: Phase-A B, 5: input tile
     __shared__ __align__(8) uint64_t mbar[6];
     __shared__ uint32_t tmem_holder;
-    __shared__ int abort_flag;
     // FP16 carrier pipeline: failure flags of the steps, read by every thread
     // right after the barrier that starts step t from slot t & 1; failures are
     // written to the slot of the step whose barrier follows them, so no thread
@@ -449,7 +448,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     } else if (w == 1) {
         const InputTile itile = input_tile(map, ncols, cbase, TILE);
         if (lane == 0) {
-            abort_flag = 0;
             if (CAR) fail[0] = fail[1] = 0;
             s_e0 = itile.e0;
             for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
@@ -494,9 +492,13 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     int e;
     int64_t ibase, istride, obase, ostride;
     map.strides(cg, ibase, istride, obase, ostride);
+    // tfail: this thread saw a bounded wait give up (or, thread 0, an issue
+    // fail); the CTA learns of it at the next __syncthreads_or, so every thread
+    // leaves the pipeline at the same barrier
+    bool tfail = false;
     {
         const bool okin = mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
-        if (!okin) atomicExch(&abort_flag, 1);
+        tfail = !okin;
         // element j of this column at sIn + (sbase + j sstride) * 16
         const int64_t sbase = map.stage == 1 ? ibase - s_e0 : (int64_t)(128 * hl + c) * (K + 1);
         const int64_t sstride = map.stage == 1 ? istride : 1;
@@ -616,15 +618,19 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     gen(0);
     tmem_wait_st();
     tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && abort_flag == 0) {
+    bool ok = __syncthreads_or(tfail) == 0;
+    if (ok && tid == 0) {
         tc_fence_after();
-        if (!issue(0)) abort_flag = 1;
-    } else if (tid == 32 && NMOD > 1) {
+        // a failed first issue: the FP16-carrier pipeline reads it from slot 0
+        // behind its first step barrier, the E4M3 pipeline at its first
+        // __syncthreads_or (every thread's MMA wait then gives up as well)
+        if (!issue(0)) {
+            if (CAR) fail[0] = 1;
+            tfail = true;
+        }
+    } else if (ok && tid == 32 && NMOD > 1) {
         prefetch_b(1);  // buffer 1 is unused so far
     }
-    __syncthreads();
-    bool ok = abort_flag == 0;
     uint32_t mph[1] = {0u};  // next phase parity of the MMA barrier mbar[2]
     uint32_t mph3 = 0u;      // next phase parity of mbar[3]
     int last_issued = 0, last_waited = -1;  // FP16 carrier, thread 0: MMA batches in flight
@@ -670,10 +676,10 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         mph[0] = (uint32_t)(((NSTEP + 1) / 2) & 1);
         mph3 = (uint32_t)((NSTEP / 2) & 1);
     } else {
-        // A failure flag raised after a step's barrier (issue() giving up) is
-        // only written once its bounded wait has run out, long after every
-        // other thread has read the flag behind that barrier; it is seen at
-        // the next step's barrier.
+        // A failure (an MMA wait or, in thread 0, issue() giving up) stays in
+        // the thread's own tfail and reaches the CTA through the next
+        // __syncthreads_or: no shared flag is written while other threads may
+        // still read it behind the same barrier.
         for (int k = 0; k < NSTEP && ok; k++) {
             if (k + 1 < NMOD) gen(k + 1);  // digits of the next modulus while this one's MMAs run
             const bool okm = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
@@ -689,12 +695,11 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 else
                     epilogue_modulus<KIND_B11, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
             } else {
-                atomicExch(&abort_flag, 1);
+                tfail = true;
             }
             tmem_wait_st();
             tc_fence_before();
-            __syncthreads();
-            if (abort_flag) {
+            if (__syncthreads_or(tfail)) {
                 ok = false;
                 break;
             }
@@ -703,7 +708,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             // every thread waited for them before this barrier)
             if (tid == 0 && k + 1 < NSTEP) {
                 tc_fence_after();
-                if (!issue(k + 1)) abort_flag = 1;
+                if (!issue(k + 1)) tfail = true;
             } else if (tid == 32 && k + 2 < NSTEP) {
                 prefetch_b(k + 2);
             }
@@ -730,7 +735,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         tc_fence_before();
         fence_async_smem();
         const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
-        ok = __syncthreads_or(bad) == 0;  // uniform decision across the CTA
+        ok = __syncthreads_or(bad | (int)(tfail && !CAR)) == 0;  // uniform decision across the CTA
         if (CAR && fail[NSTEP & 1]) ok = false;  // a failed wait in the last pipeline step
         const uint32_t idescA = instr_desc(128, PA_N, 0);
         const uint64_t adescA = smem_desc(smem_u32(sStage), 128, PA_ROWB);
@@ -822,11 +827,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             tc_fence_after();
             if (okA && okB)
                 for (int bi = qd + 4; bi < nb; bi += 4) do_block(bi);
-            if (!(okA && okB)) atomicExch(&abort_flag, 1);
             tmem_wait_st();
             tc_fence_before();
-            __syncthreads();
-            if (abort_flag) ok = false;
+            if (__syncthreads_or(!(okA && okB))) ok = false;
         }
     }
     if (!ok && tid == 0) {

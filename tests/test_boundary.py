@@ -93,3 +93,25 @@ def test_host_constants_fp32_variant_match_oracle(lib):
     assert [list(ws[3 * k:3 * k + 3]) for k in range(6)] == C.W_SLICES_FP32
     assert M.value == C.M_FP32
     assert lib.obfft_host_crt_constants32(None, us, ws, ctypes.byref(M)) == 1
+
+
+def test_huge_axis_lengths_rejected_quickly(lib):
+    """Axis lengths far above 64 x 64 (a large prime, one near 1e9, and one whose
+    square overflows int64) are rejected before any split search or any GPU
+    call, by both plan creation and the no-allocation entry point."""
+    import time
+    h = ctypes.c_void_p()
+    t0 = time.perf_counter()
+    for n in ((1 << 61) - 1, 999999937, 4097, 65 * 64):
+        for mode in (0, 1, 2):
+            assert lib.obfft_plan_create(ctypes.byref(h), n, 1, 1, 1, mode) == 2
+        # fake, aligned, distinct pointers: rejected before any use of them
+        assert lib.obfft_exec_fp64_noalloc(ctypes.c_void_p(256), ctypes.c_void_p(512), 2, n, 2, -1, None) == 2
+        assert b"factor" in lib.obfft_last_error()
+    # three axes whose product wraps around int64 but each factors: the grid
+    # is still refused as too large, not accepted through the wrapped product
+    assert lib.obfft_exec_fp64_noalloc(ctypes.c_void_p(256), ctypes.c_void_p(512), 4096, 4096, 4096, -1, None) == 2
+    assert b"exceeds" in lib.obfft_last_error()
+    assert time.perf_counter() - t0 < 1.0
+    dims = (ctypes.c_int64 * 6)(8, 8, 8, 8, (1 << 61) - 1, 8)
+    assert lib.obfft_plan_create_many(ctypes.byref(h), 2, dims, 0) == 2

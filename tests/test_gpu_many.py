@@ -121,3 +121,32 @@ def test_many_random_grids_match_oracle(mode):
         got = outs[i].cpu().numpy()
         assert bits_equal(got, want), (i, d) + (mismatch_report(got, want),)
     pm.close()
+
+
+def test_many_rejects_overlapping_ranges():
+    """The groups run as concurrent graph branches, so an output that overlaps
+    another grid's input or output is refused with OBFFT_ERR_ARG (inputs may
+    share memory)."""
+    from paper_2606_23698_gb300 import ObfftError, _lib
+    dims = [(8, 8, 8), (4, 4, 16)]
+    pm = _lib.obfft_plan_create_many(dims, _lib.OBFFT_MODE_FP64_NATIVE)
+    try:
+        buf = torch.zeros(4096, dtype=torch.complex128, device="cuda")
+        base = buf.data_ptr()
+        s = torch.cuda.current_stream().cuda_stream
+        e = 16  # bytes per complex128
+        ok = ([base, base + 1024 * e], [base + 2048 * e, base + 2560 * e])
+        _lib.obfft_exec_many(pm, ok[0], ok[1], -1, s)
+        torch.cuda.synchronize()
+        shared_in = ([base, base], [base + 2048 * e, base + 2560 * e])  # one input read by both
+        _lib.obfft_exec_many(pm, shared_in[0], shared_in[1], -1, s)
+        torch.cuda.synchronize()
+        bad = [([base, base + 1024 * e], [base + 2048 * e, base + 100 * e]),    # out 1 inside in 0
+               ([base, base + 1024 * e], [base + 2048 * e, base + 2300 * e]),   # out 1 overlaps out 0
+               ([base, base + 1024 * e], [base + 1200 * e, base + 3000 * e])]   # out 0 overlaps in 1
+        for ins, outs in bad:
+            with pytest.raises(ObfftError) as ei:
+                _lib.obfft_exec_many(pm, ins, outs, -1, s)
+            assert "overlap" in str(ei.value)
+    finally:
+        _lib.obfft_destroy(pm)

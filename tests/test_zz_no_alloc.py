@@ -48,7 +48,10 @@ def test_noalloc_matches_regular_entry_on_two_calls(lib):
     warm_out = torch.empty_like(warm_in)
     _noalloc(lib, warm_in, warm_out, (2, 2, 2), -1)
     cases = [((32, 48, 64), -1, S.complex_uniform(11, (32, 48, 64))),
-             ((16, 128, 96), +1, S.complex_gaussian(12, (16, 128, 96)))]
+             ((16, 128, 96), +1, S.complex_gaussian(12, (16, 128, 96))),
+             # a length-1 first axis: the pass is a device-to-device copy
+             ((16, 24, 1), -1, S.complex_uniform(13, (16, 24, 1))),
+             ((1, 1, 1), +1, S.complex_uniform(14, (1, 1, 1)))]
     for shape, dir, xh in cases:
         x = xh.to("cuda").contiguous()
         want = _regular(lib, x, shape, dir)
