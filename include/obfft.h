@@ -131,6 +131,34 @@ obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, void *const *
                              void *stream);
 
 /*
+ * Run the axis passes first_axis, first_axis - 1, ..., last_axis of a
+ * one-grid plan (2 >= first_axis >= last_axis >= 0; obfft_exec is (2, 0)).
+ * Each pass transforms the lines of the contiguous axis (Bailey six-step,
+ * Algorithm 1) and writes them rotated, [batch][A1][A2][n_axis] ->
+ * [batch][n_axis][A1][A2], so the data layouts are: before the pass over
+ * axis 2 (natural) [batch][n0][n1][n2]; before axis 1 [batch][n2][n0][n1];
+ * before axis 0 [batch][n1][n2][n0]; after axis 0 [batch][n0][n1][n2].
+ * `in` must hold the layout of the first pass.  Used by the slab
+ * decomposition of one grid over several GPUs (local passes over axes 2 and
+ * 1, an all-to-all exchange, then the pass over axis 0; the paper has no
+ * multi-GPU design).  Same pointer rules and errors as obfft_exec.
+ */
+obfft_status obfft_exec_axes(obfft_plan p, int first_axis, int last_axis, const void *in, void *out, int dir,
+                             void *stream);
+
+/*
+ * Device-to-device block transpose used around the all-to-all exchange of
+ * the slab decomposition (not part of the paper): `src` holds `nblocks`
+ * contiguous blocks of `rows` rows of `row_bytes` bytes; `dst` receives, for
+ * each row r, the rows r of blocks 0 .. nblocks-1 side by side:
+ *   dst[r][k][0 .. row_bytes) = src[k][r][0 .. row_bytes).
+ * Device pointers, disjoint ranges; asynchronous on `stream`.  OBFFT_ERR_ARG
+ * for NULL, equal or overlapping buffers or a bad geometry.
+ */
+obfft_status obfft_transpose_blocks(const void *src, void *dst, int64_t nblocks, int64_t rows, int64_t row_bytes,
+                                    void *stream);
+
+/*
  * Run ONE Bailey stage of ONE axis pass on the current contents of `in`
  * (debug / parity entry): stage 1 or 2 of the pass over axis `axis`.  `in`
  * holds the pass input laid out [batch][A1][A2][n_axis] (axis contiguous),
@@ -144,6 +172,46 @@ obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, void *const *
  */
 obfft_status obfft_exec_stage(obfft_plan p, int axis, int stage, const void *in, void *out, int dir,
                               void *stream);
+
+/*
+ * Integer dump of one Bailey stage, for parity checks of every integer step
+ * against an independent implementation (Algorithm 1, one half: the
+ * deconstruction, the residue GEMMs, the combine; Algorithm 2: the CRT with
+ * Phase A, the Kulisch sum and the two-sided lift).  Runs stage `stage` of
+ * the pass over `axis` exactly as obfft_exec_stage (same output in `out`) and
+ * writes, for the logical columns [col0, col0 + ncols) of that stage, the
+ * stage's integers into the device buffer `dump` (zeroed first by the call).
+ * A logical column is one length-K DFT input vector: stage 1, c = line * p +
+ * j1 (K = q, elements j2); stage 2, c = k2 * L + line (K = p, elements j1),
+ * L = lines of the pass.  K outputs per column.  Sections (byte offsets from
+ * obfft_debug_layout; nm moduli: 12, or 6 for OBFFT_MODE_FP32):
+ *   [0] int32  e[ncols]                   column exponent (x~ = RNE(x 2^(52 - e)),
+ *                                          2^(23 - e) for OBFFT_MODE_FP32)
+ *   [1] int64  xt[ncols][K][2]            x~ of each element (Re, Im)
+ *   [2] uint16 def[ncols][K][nm][3]       INT8 mode: the residue products D, E,
+ *                                          F mod m_k (Karatsuba, canonical);
+ *                                          other modes: zero (real-form products)
+ *   [3] uint16 res[ncols][K][2][nm]       the CRT operand of each output part and
+ *                                          modulus: INT8 the canonical v_k; the
+ *                                          tensor-core modes the offset residue
+ *                                          r + 1024, r = v_k (mod m_k), |r| <= m_k/2 + 1
+ *   [4] uint32 acc[ncols][K][2][na]       tensor-core modes: the Phase-A
+ *                                          accumulators as FP32 bit patterns
+ *                                          0x4B000000 + P_s (s < S) then + Q_t
+ *                                          (t < F) of the offset residues (na =
+ *                                          21, or 11 for OBFFT_MODE_FP32); INT8: zero
+ *   [5] int64  zhat[ncols][K][2]          the lift quotient the kernel used
+ *   [6] uint32 R[ncols][K][2][4]          the centred CRT value R (|R| < M/2), the
+ *                                          integer the output is rounded from:
+ *                                          128-bit two's complement, little-endian
+ *                                          words
+ * offsets[7] is the total size.  Native modes have no integer stages
+ * (OBFFT_ERR_ARG).  Errors as obfft_exec_stage, plus OBFFT_ERR_ARG for
+ * columns outside the stage.
+ */
+obfft_status obfft_debug_layout(int mode, int K, int Kout, int64_t ncols, int64_t *offsets /* [8] */);
+obfft_status obfft_exec_debug(obfft_plan p, int axis, int stage, const void *in, void *out, int dir, int64_t col0,
+                              int64_t ncols, void *dump, void *stream);
 
 /*
  * Transform from host memory to host memory (one-grid plans): in and out are

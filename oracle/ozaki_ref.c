@@ -377,6 +377,8 @@ typedef struct {
     int64_t *Q;        /* [ncols][Kout][2][S_FRAC32] lift partials        */
     int64_t *zhat;     /* [ncols][Kout][2]                                */
     int64_t *R;        /* [ncols][Kout][2]           lifted R (|R| < 2^63) */
+    int32_t *col_exp;  /* [ncols]                    column exponent e       */
+    int64_t *xt;       /* [ncols][K][2]              deconstructed integers  */
 } ob_dump32;
 
 /* RNE(R * 2^e) to binary32, gradual underflow (quantum 2^-149), overflow to
@@ -432,6 +434,8 @@ int64_t ob_ref_stage32(int64_t ncols, int K, int Kout,
         int e = amax > 0.0 ? ilogb(amax) : 0;
         int64_t xt[2 * 64];
         for (int j = 0; j < 2 * K; j++) xt[j] = (int64_t)rint(ldexp((double)xc[j], 23 - e));
+        if (dump && dump->col_exp) dump->col_exp[col] = e;
+        if (dump && dump->xt) memcpy(dump->xt + col * (int64_t)K * 2, xt, sizeof(int64_t) * 2 * K);
 
         for (int k = 0; k < Kout; k++) {
             const int64_t *Fk = F + (int64_t)k * K * 2;

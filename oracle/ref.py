@@ -52,7 +52,7 @@ class _Consts32(ctypes.Structure):
 
 
 class _Dump32(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in ("v", "P", "Q", "zhat", "R")]
+    _fields_ = [(n, ctypes.c_void_p) for n in ("v", "P", "Q", "zhat", "R", "col_exp", "xt")]
 
 
 class _Dump(ctypes.Structure):
@@ -201,7 +201,8 @@ def stage32(cols: np.ndarray, Ftab: np.ndarray, group: np.ndarray | None = None,
                       P=np.zeros((ncols, Kout, 2, 8), np.int64),
                       Q=np.zeros((ncols, Kout, 2, 3), np.int64),
                       zhat=np.zeros((ncols, Kout, 2), np.int64),
-                      R=np.zeros((ncols, Kout, 2), np.int64))
+                      R=np.zeros((ncols, Kout, 2), np.int64),
+                      col_exp=np.zeros(ncols, np.int32), xt=np.zeros((ncols, K, 2), np.int64))
         for k, a in arrays.items():
             setattr(d, k, a.ctypes.data)
     cst = consts32()

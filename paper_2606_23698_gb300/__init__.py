@@ -12,3 +12,4 @@ from ._lib import (OBFFT_MODE_FP8, OBFFT_MODE_INT8, OBFFT_MODE_FP64_NATIVE, MODE
                    obfft_last_error, obfft_version)
 from .api import Plan, PlanMany, fft3, ifft3  # noqa: F401
 from .autograd import ObFFT3, fft3_autograd  # noqa: F401
+from .slab import SlabPlan, slab_geometry  # noqa: F401

@@ -38,7 +38,8 @@ EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_s
            "obfft_version", "obfft_host_twiddle", "obfft_host_crt_constants",
            "obfft_exec_fp64_noalloc", "obfft_plan_status", "obfft_selftest_bounded_wait",
            "obfft_exec_host", "obfft_host_twiddle32", "obfft_host_crt_constants32",
-           "obfft_ablation_phase_b", "obfft_ablation_residues")
+           "obfft_ablation_phase_b", "obfft_ablation_residues", "obfft_exec_axes", "obfft_transpose_blocks",
+           "obfft_debug_layout", "obfft_exec_debug")
 
 _lib = None
 
@@ -64,10 +65,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_exec_host.argtypes = [vp, vp, vp, i32, vp]
     L.obfft_exec_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp]
     L.obfft_exec_stage.argtypes = [vp, i32, i32, vp, vp, i32, vp]
+    L.obfft_exec_axes.argtypes = [vp, i32, i32, vp, vp, i32, vp]
+    L.obfft_transpose_blocks.argtypes = [vp, vp, i64, i64, i64, vp]
+    L.obfft_debug_layout.argtypes = [i32, i32, i32, i64, ctypes.POINTER(i64)]
+    L.obfft_debug_layout.restype = i32
+    L.obfft_exec_debug.argtypes = [vp, i32, i32, vp, vp, i32, i64, i64, vp, vp]
+    L.obfft_exec_debug.restype = i32
     L.obfft_destroy.argtypes = [vp]
     L.obfft_plan_get_splits.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     for f in ("obfft_plan_create", "obfft_plan_create_many", "obfft_exec", "obfft_exec_host", "obfft_exec_many",
-              "obfft_exec_stage", "obfft_destroy", "obfft_plan_get_splits"):
+              "obfft_exec_stage", "obfft_destroy", "obfft_plan_get_splits", "obfft_exec_axes",
+              "obfft_transpose_blocks"):
         getattr(L, f).restype = i32
     L.obfft_last_error.restype = ctypes.c_char_p
     L.obfft_last_error.argtypes = []
@@ -133,6 +141,28 @@ def obfft_exec_many(plan: int, in_ptrs, out_ptrs, dir: int, stream: int = 0) -> 
 def obfft_exec_stage(plan: int, axis: int, stage: int, in_ptr: int, out_ptr: int, dir: int,
                      stream: int = 0) -> None:
     check(load().obfft_exec_stage(plan, axis, stage, in_ptr, out_ptr, dir, stream))
+
+
+def obfft_exec_axes(plan: int, first_axis: int, last_axis: int, in_ptr: int, out_ptr: int, dir: int,
+                    stream: int = 0) -> None:
+    check(load().obfft_exec_axes(plan, first_axis, last_axis, in_ptr, out_ptr, dir, stream))
+
+
+def obfft_transpose_blocks(src_ptr: int, dst_ptr: int, nblocks: int, rows: int, row_bytes: int,
+                           stream: int = 0) -> None:
+    check(load().obfft_transpose_blocks(src_ptr, dst_ptr, nblocks, rows, row_bytes, stream))
+
+
+def obfft_debug_layout(mode: int, K: int, Kout: int, ncols: int):
+    """Byte offsets of the seven dump sections and the total size (offsets[7])."""
+    off = (ctypes.c_int64 * 8)()
+    check(load().obfft_debug_layout(mode, K, Kout, ncols, off))
+    return list(off)
+
+
+def obfft_exec_debug(plan: int, axis: int, stage: int, in_ptr: int, out_ptr: int, dir: int, col0: int,
+                     ncols: int, dump_ptr: int, stream: int = 0) -> None:
+    check(load().obfft_exec_debug(plan, axis, stage, in_ptr, out_ptr, dir, col0, ncols, dump_ptr, stream))
 
 
 def obfft_destroy(plan: int) -> None:

@@ -281,15 +281,17 @@ __device__ __forceinline__ double kulisch_pack_fp8(const uint32_t *wv, const Mod
 // general finish is needed: lift near a rounding boundary, |R| < 2^64, or a
 // result that is subnormal or overflows; Rw (R = E - ebias - zhat M mod 2^128)
 // and near_out then feed kulisch_finish_general.
+// zhat_out (debug builds): receives the lift quotient.
 __device__ __forceinline__ double lift_pack_fast(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
                                                  const uint32_t *wq, const ModConsts &mc, int et,
                                                  const uint32_t (&ebias)[4], uint64_t zbias, bool &slow,
-                                                 uint32_t (&Rw)[4], bool &near_out) {
+                                                 uint32_t (&Rw)[4], bool &near_out, uint32_t *zhat_out = nullptr) {
     uint64_t z = (uint64_t)wq[0] + (uint64_t)wq[1] * 256u + (uint64_t)wq[2] * 65536u +
                  (uint64_t)wq[3] * 16777216u + ((uint64_t)wq[4] << 32) + ((uint64_t)wq[5] << 40);
     z -= zbias;
     const uint64_t zr = z + (1ull << 47);
     const uint32_t zhat = (uint32_t)(zr >> 48);
+    if (zhat_out) *zhat_out = zhat;
     const uint64_t frac = zr & ((1ull << 48) - 1);
     uint64_t p0 = (uint64_t)zhat * mc.M32[0];
     uint64_t p1 = (uint64_t)zhat * mc.M32[1] + (p0 >> 32);
@@ -341,7 +343,8 @@ __device__ __forceinline__ double lift_pack_fast(uint32_t w0, uint32_t w1, uint3
 // result equals kulisch_pack_fp8's bit for bit.
 __device__ __forceinline__ double kulisch_pack_fp8_fast(const uint32_t *wv, const ModConsts &mc, int et,
                                                         const uint32_t (&ebias)[4], uint64_t zbias, bool &slow,
-                                                        uint32_t (&Rw)[4], bool &near_out) {
+                                                        uint32_t (&Rw)[4], bool &near_out,
+                                                        uint32_t *zhat_out = nullptr) {
     uint64_t a0 = (uint64_t)wv[0];
     a0 += (uint64_t)wv[1] * 256u;
     a0 += (uint64_t)wv[2] * 65536u;
@@ -364,7 +367,21 @@ __device__ __forceinline__ double kulisch_pack_fp8_fast(const uint32_t *wv, cons
     const uint32_t w2 = (uint32_t)t;
     t = (t >> 32) + a3;
     const uint32_t w3 = (uint32_t)t;
-    return lift_pack_fast(w0, w1, w2, w3, wv + 15, mc, et, ebias, zbias, slow, Rw, near_out);
+    return lift_pack_fast(w0, w1, w2, w3, wv + 15, mc, et, ebias, zbias, slow, Rw, near_out, zhat_out);
+}
+
+// The centred CRT value from the lifted words of lift_pack_fast: the
+// two-sided correction where the lift was near a rounding boundary (as
+// kulisch_finish_general applies it before packing).
+__device__ __forceinline__ i128 lift_centre(const uint32_t *Rw, bool near, const ModConsts &mc) {
+    i128 R = (i128)((((u128)Rw[3]) << 96) | (((u128)Rw[2]) << 64) | (((u128)Rw[1]) << 32) | (u128)Rw[0]);
+    if (near) {
+        const u128 M = u128_from_words(mc.M32);
+        const i128 half = (i128)u128_from_words(mc.halfM32);
+        if (R >= half) R -= (i128)M;
+        if (R < -half) R += (i128)M;
+    }
+    return R;
 }
 
 // General finish from R = E - bias - zhat M (mod 2^128): the two-sided

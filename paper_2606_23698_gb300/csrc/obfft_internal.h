@@ -152,6 +152,37 @@ struct obfft_plan_s {
 };
 
 namespace obfft {
+// Integer dump of one Bailey stage (obfft_exec_debug): device pointers into the
+// caller's buffer (sections as in include/obfft.h), written by the DBG
+// instantiations of the stage kernels for the logical columns
+// [col0, col0 + ncols).  Logical column: stage 1, c = line * p + j1 (the
+// kernel's own column index); stage 2, c = k2 * L + line (the kernel pads
+// each k2 group of columns to Lpad).
+struct DebugDump {
+    int32_t *e = nullptr;      // [ncols]                    column exponent
+    int64_t *xt = nullptr;     // [ncols][K][2]              deconstructed integers (Re, Im)
+    uint16_t *def = nullptr;   // [ncols][Kout][nmod][3]     INT8: D, E, F mod m_k (canonical)
+    uint16_t *res = nullptr;   // [ncols][Kout][2][nmod]     the CRT operands (Re, Im)
+    uint32_t *acc = nullptr;   // [ncols][Kout][2][nacc]     Phase-A accumulator words (FP32 bits)
+    int64_t *zhat = nullptr;   // [ncols][Kout][2]           lift quotient
+    uint32_t *R = nullptr;     // [ncols][Kout][2][4]        centred CRT value, 128-bit two's complement
+    int64_t col0 = 0, ncols = 0;
+    int K = 0, Kout = 0, nmod = 0, nacc = 0;
+    int stage = 1;
+    int64_t L = 0, Lpad = 0;
+    // dump row of the kernel's column c, or -1 when c is not dumped
+    __host__ __device__ __forceinline__ int64_t row(int64_t c) const {
+        const int64_t lc = stage == 1 ? c : (c / Lpad) * L + (c % Lpad);
+        const int64_t d = lc - col0;
+        return (d >= 0 && d < ncols) ? d : -1;
+    }
+    __host__ __device__ __forceinline__ void put_R128(int64_t d, int k, int part, uint32_t r0, uint32_t r1,
+                                                      uint32_t r2, uint32_t r3) const {
+        uint32_t *p = R + ((d * Kout + k) * 2 + part) * 4;
+        p[0] = r0; p[1] = r1; p[2] = r2; p[3] = r3;
+    }
+};
+
 // error reporting
 obfft_status set_error(obfft_status st, const std::string &msg);
 AxisTables *get_tables(obfft_plan p, int n, int pp, int qq, int dir);
@@ -164,16 +195,19 @@ struct StageGeom {
     int n, p, q;
 };
 cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const StageGeom &g,
-                              int stage, const double2 *in, double2 *out, cudaStream_t s);
+                              int stage, const double2 *in, double2 *out, cudaStream_t s,
+                              const DebugDump *dbg = nullptr);
 cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
-                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
+                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s,
+                             const DebugDump *dbg = nullptr);
 cudaError_t launch_stage_fp16(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
-                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s);
+                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s,
+                              const DebugDump *dbg = nullptr);
 std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups, int K, const int *moduli,
                                        int nmod);
 // FP32-precision variant
 cudaError_t launch_stage_fp32(const AxisTables &t, const void *pab, int *status, const StageGeom &g, int stage,
-                              const float2 *in, float2 *out, cudaStream_t s);
+                              const float2 *in, float2 *out, cudaStream_t s, const DebugDump *dbg = nullptr);
 cudaError_t fp32_upload_constants();  // once per device, outside any stream capture
 size_t fp32_smem_bytes(int Kout, int npad);
 std::vector<uint8_t> build_phase_a_b32();

@@ -409,8 +409,8 @@ std::vector<uint8_t> build_fp16_planes(const std::vector<int64_t> &F, int groups
 }
 
 // Phase A B-matrix: 48 rows (Re: 15 u-slices, 6 w-slices, 3 zero; Im: same)
-// x 32 K (Re residues 0..11, Im residues 12..23, 8 zero), FP16, K-major
-// canonical layout (LBO 128, SBO 512).
+// x 32 K (the Re and Im residues of modulus k at K = 2k and 2k + 1, then 8
+// zero), FP16, K-major canonical layout (LBO 128, SBO 512).
 std::vector<uint8_t> build_phase_a_b() {
     ModConsts mc;
     make_mod_consts(&mc);
@@ -419,8 +419,8 @@ std::vector<uint8_t> build_phase_a_b() {
         int part = n / 24, col = n % 24;
         for (int kk = 0; kk < 32; kk++) {
             int val = 0;
-            if (kk < 24 && kk / 12 == part && col < 21) {
-                int k = kk % 12;
+            if (kk < 24 && (kk & 1) == part && col < 21) {
+                int k = kk >> 1;
                 val = col < S_RAW ? mc.us[k][col] : mc.ws[k][col - S_RAW];
             }
             uint16_t h = f16_of_small(val);
@@ -951,12 +951,16 @@ static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, i
     return run_stage_geom(P, gd.ax[axis], pass_geom(gd, batch, axis), stage, in, out, dir, s);
 }
 
+// The axis passes first_axis, first_axis - 1, ..., last_axis (the full
+// transform: 2 down to 0), each reading lines of its (contiguous) axis and
+// writing them rotated, so that the next axis is contiguous.
 static obfft_status exec_grid(obfft_plan P, const GridDesc &gd, int64_t batch, const void *in, void *out,
-                              int dir, cudaStream_t s, void *scratch_override = nullptr) {
+                              int dir, cudaStream_t s, void *scratch_override = nullptr, int first_axis = 2,
+                              int last_axis = 0) {
     const void *src = in;
     void *scratch = scratch_override ? scratch_override : P->scratch;
     const int64_t total = gd.n[0] * gd.n[1] * gd.n[2] * batch;
-    for (int axis = 2; axis >= 0; axis--) {
+    for (int axis = first_axis; axis >= last_axis; axis--) {
         const AxisPlan &ap = gd.ax[axis];
         if (ap.n == 1) {
             // length-1 axis: identity; the axis rotation [B][A1][A2][1] -> [B][1][A1][A2]
@@ -1253,6 +1257,126 @@ extern "C" obfft_status obfft_exec_many(obfft_plan p, const void *const *ins, vo
     }
     cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
     if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_exec_axes(obfft_plan p, int first_axis, int last_axis, const void *in, void *out,
+                                        int dir, void *stream) {
+    if (!p) return set_error(OBFFT_ERR_ARG, "plan is NULL");
+    if (dir != -1 && dir != 1) return set_error(OBFFT_ERR_ARG, "dir must be -1 or +1");
+    if (first_axis < 0 || first_axis > 2 || last_axis < 0 || last_axis > first_axis)
+        return set_error(OBFFT_ERR_ARG, "need 2 >= first_axis >= last_axis >= 0");
+    obfft_status st = check_ptrs(in, out);
+    if (st != OBFFT_OK) return st;
+    if (p->grids.size() != 1) return set_error(OBFFT_ERR_ARG, "plan has several grids");
+    const size_t bytes =
+        (size_t)(p->grids[0].n[0] * p->grids[0].n[1] * p->grids[0].n[2] * p->batch) * elem_bytes(p->mode);
+    const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+    if (a < b + bytes && b < a + bytes) return set_error(OBFFT_ERR_ARG, "in and out overlap");
+    return exec_grid(p, p->grids[0], p->batch, in, out, dir, (cudaStream_t)stream, nullptr, first_axis, last_axis);
+}
+
+extern "C" obfft_status obfft_transpose_blocks(const void *src, void *dst, int64_t nblocks, int64_t rows,
+                                               int64_t row_bytes, void *stream) {
+    if (!src || !dst || src == dst) return set_error(OBFFT_ERR_ARG, "src/dst NULL or equal");
+    if (nblocks < 1 || rows < 0 || row_bytes < 1) return set_error(OBFFT_ERR_ARG, "bad block geometry");
+    const size_t total = (size_t)nblocks * (size_t)rows * (size_t)row_bytes;
+    const uintptr_t a = (uintptr_t)src, b = (uintptr_t)dst;
+    if (a < b + total && b < a + total) return set_error(OBFFT_ERR_ARG, "src and dst overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    // block k of the source (rows x row_bytes, contiguous) becomes column
+    // block k of the destination rows (pitch nblocks x row_bytes)
+    for (int64_t k = 0; k < nblocks && rows > 0; k++) {
+        cudaError_t e = cudaMemcpy2DAsync((char *)dst + k * row_bytes, (size_t)(nblocks * row_bytes),
+                                          (const char *)src + k * rows * row_bytes, (size_t)row_bytes,
+                                          (size_t)row_bytes, (size_t)rows, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("block copy: ") + cudaGetErrorString(e));
+    }
+    return OBFFT_OK;
+}
+
+// Byte offsets of the sections of an obfft_exec_debug dump (16-byte aligned).
+static void debug_layout(int64_t ncols, int K, int Kout, int nmod, int nacc, int64_t off[8]) {
+    auto al = [](int64_t v) { return (v + 15) & ~(int64_t)15; };
+    int64_t o = 0;
+    off[0] = o; o = al(o + ncols * 4);                               // e
+    off[1] = o; o = al(o + ncols * K * 2 * 8);                       // xt
+    off[2] = o; o = al(o + ncols * Kout * nmod * 3 * 2);             // def
+    off[3] = o; o = al(o + ncols * Kout * 2 * nmod * 2);             // res
+    off[4] = o; o = al(o + ncols * Kout * 2 * nacc * 4);             // acc
+    off[5] = o; o = al(o + ncols * Kout * 2 * 8);                    // zhat
+    off[6] = o; o = al(o + ncols * Kout * 2 * 4 * 4);                // R
+    off[7] = o;
+}
+
+static bool mode_has_integers(int mode) {
+    return mode == OBFFT_MODE_FP8 || mode == OBFFT_MODE_INT8 || mode == OBFFT_MODE_FP16 || mode == OBFFT_MODE_FP32;
+}
+
+extern "C" obfft_status obfft_debug_layout(int mode, int K, int Kout, int64_t ncols, int64_t *offsets) {
+    if (!offsets || !mode_has_integers(mode) || K < 1 || Kout < 1 || ncols < 0 || K > KMAX || Kout > KMAX)
+        return set_error(OBFFT_ERR_ARG, "bad mode (native modes have no integer stages), size or NULL offsets");
+    const int nm = mode == OBFFT_MODE_FP32 ? NMOD32 : NMOD;
+    const int na = mode == OBFFT_MODE_FP32 ? S_RAW32 + S_FRAC32 : S_RAW + S_FRAC;
+    debug_layout(ncols, K, Kout, nm, na, offsets);
+    return OBFFT_OK;
+}
+
+extern "C" obfft_status obfft_exec_debug(obfft_plan p, int axis, int stage, const void *in, void *out, int dir,
+                                         int64_t col0, int64_t ncols, void *dump, void *stream) {
+    if (!p || axis < 0 || axis > 2 || (stage != 1 && stage != 2) || !dump) return set_error(OBFFT_ERR_ARG, "bad argument");
+    if (dir != -1 && dir != 1) return set_error(OBFFT_ERR_ARG, "dir must be -1 or +1");
+    if (!mode_has_integers(p->mode)) return set_error(OBFFT_ERR_ARG, "native modes have no integer stages to dump");
+    if (p->grids.size() != 1) return set_error(OBFFT_ERR_ARG, "plan has several grids");
+    obfft_status st = check_ptrs(in, out);
+    if (st != OBFFT_OK) return st;
+    const GridDesc &gd = p->grids[0];
+    const AxisPlan &ap = gd.ax[axis];
+    if (ap.n == 1) return set_error(OBFFT_ERR_ARG, "axis of length 1 has no stages");
+    const StageGeom g = pass_geom(gd, p->batch, axis);
+    const int K = stage == 1 ? ap.q : ap.p;
+    const int64_t total_cols = stage == 1 ? g.L * ap.p : g.L * ap.q;
+    if (col0 < 0 || ncols < 1 || col0 + ncols > total_cols)
+        return set_error(OBFFT_ERR_ARG, "dumped columns outside [0, " + std::to_string(total_cols) + ")");
+    AxisTables *t = get_tables(p, ap.n, ap.p, ap.q, dir);
+    if (!t) return set_error(OBFFT_ERR_INTERNAL, "missing tables");
+    const int nm = p->mode == OBFFT_MODE_FP32 ? NMOD32 : NMOD;
+    const int na = p->mode == OBFFT_MODE_FP32 ? S_RAW32 + S_FRAC32 : S_RAW + S_FRAC;
+    int64_t off[8];
+    debug_layout(ncols, K, K, nm, na, off);
+    char *b = (char *)dump;
+    DebugDump d;
+    d.e = (int32_t *)(b + off[0]);
+    d.xt = (int64_t *)(b + off[1]);
+    d.def = (uint16_t *)(b + off[2]);
+    d.res = (uint16_t *)(b + off[3]);
+    d.acc = (uint32_t *)(b + off[4]);
+    d.zhat = (int64_t *)(b + off[5]);
+    d.R = (uint32_t *)(b + off[6]);
+    d.col0 = col0;
+    d.ncols = ncols;
+    d.K = K;
+    d.Kout = K;
+    d.nmod = nm;
+    d.nacc = na;
+    d.stage = stage;
+    d.L = g.L;  // the launchers set Lpad (their own tile padding)
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(dump, 0, (size_t)off[7], s);
+    if (e == cudaSuccess) {
+        const double2 *i2 = (const double2 *)in;
+        double2 *o2 = (double2 *)out;
+        switch (p->mode) {
+            case OBFFT_MODE_INT8: e = launch_stage_int8(*t, p->d_consts, g, stage, i2, o2, s, &d); break;
+            case OBFFT_MODE_FP8: e = launch_stage_fp8(*t, p->d_consts, p->d_pab, p->d_status, g, stage, i2, o2, s, &d); break;
+            case OBFFT_MODE_FP16: e = launch_stage_fp16(*t, p->d_consts, p->d_pab, p->d_status, g, stage, i2, o2, s, &d); break;
+            case OBFFT_MODE_FP32:
+                e = launch_stage_fp32(*t, p->d_pab, p->d_status, g, stage, (const float2 *)in, (float2 *)out, s, &d);
+                break;
+            default: e = cudaErrorInvalidValue;
+        }
+    }
+    if (e != cudaSuccess) return set_error(OBFFT_ERR_CUDA, std::string("debug launch: ") + cudaGetErrorString(e));
     return OBFFT_OK;
 }
 

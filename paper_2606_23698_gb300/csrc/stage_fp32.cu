@@ -99,7 +99,9 @@ __device__ __forceinline__ float pack32_rne(int64_t R, int et) {
 
 // Phase B of one output: 8 u-slice and 3 w-slice accumulators (FP32 bit
 // patterns 2^23 + P), the lift, the offset and the pack.
-__device__ __forceinline__ float crt_pack32(const uint32_t *w, int et, uint64_t M, int64_t halfM) {
+// zhat_out / R_out (debug builds): the lift quotient and the centred value.
+__device__ __forceinline__ float crt_pack32(const uint32_t *w, int et, uint64_t M, int64_t halfM,
+                                            int64_t *zhat_out = nullptr, int64_t *R_out = nullptr) {
     // sum_s (bits - 0x4B000000) 256^s = sum_s bits 256^s - 0x4B000000 sum_s 256^s (mod 2^64)
     constexpr uint64_t EB = 0x4B000000ull * 0x0101010101010101ull;
     constexpr uint64_t ZB = 0x4B000000ull * 0x010101ull;
@@ -112,6 +114,8 @@ __device__ __forceinline__ float crt_pack32(const uint32_t *w, int et, uint64_t 
     int64_t R = (int64_t)(E - zhat * M);
     if (R >= halfM) R -= (int64_t)M;
     if (R < -halfM) R += (int64_t)M;
+    if (zhat_out) *zhat_out = (int64_t)zhat;
+    if (R_out) *R_out = R - RES_OFFSET;
     return pack32_rne(R - RES_OFFSET, et);
 }
 
@@ -206,11 +210,12 @@ __device__ __forceinline__ void prefetch_input_tile32(const ColMapT &map, const 
 // with block-diagonal constants; quarter-warp group qd works on line
 // qd / (4 / LPV) only; a CTA covers 128 LPV lines.
 // ---------------------------------------------------------------------------
-template <int NPAD, int LPV>
+// DBG: also write the stage's integers of the dumped columns to `dbg`.
+template <int NPAD, int LPV, bool DBG>
 __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     stage_fp32_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab, ColMapT map,
                       int64_t ncols, int K, int Kout, const float2 *__restrict__ in, float2 *__restrict__ out,
-                      int *status, int pf_ahead, int tma_in) {
+                      int *status, int pf_ahead, int tma_in, DebugDump dbg) {
     constexpr int EPT = NPAD / 4, OPT = NPAD / 4;
     constexpr uint32_t PLANE_B = NPAD * NPAD * 2, BUF_PLANES = 8, SBO = 16 * NPAD;
     constexpr uint32_t ACC = 4 * NPAD;  // columns of one accumulator set (two classes, Re | Im)
@@ -305,6 +310,18 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
 #pragma unroll
         for (int jj = 0; jj < EPT; jj++) xt[jj] = scale_round2(x[jj], e);
     }
+    const int64_t drow = DBG && cvalid ? dbg.row(cg) : -1;
+    if (DBG && drow >= 0) {
+        if (qd == QPL * hl) dbg.e[drow] = e;
+#pragma unroll
+        for (int jj = 0; jj < EPT; jj++) {
+            const int j = EPT * qd + jj - KS * hl;
+            if (j < K) {
+                dbg.xt[(drow * K + j) * 2] = (int64_t)xt[jj].x;
+                dbg.xt[(drow * K + j) * 2 + 1] = (int64_t)xt[jj].y;
+            }
+        }
+    }
 
     // FP16 residues of x_R and x_I for modulus k into A buffer (k & 1)
     auto gen = [&](int k) {
@@ -370,6 +387,14 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
                 const float2 cv = offset_residue2(sum, nm2, im2);
                 const uint32_t hv = f16x2(cv.x, cv.y);  // exact: offset residues in [2, 2046]
                 const int k0 = qd * OPT + 2 * o2;
+                if (DBG && drow >= 0) {
+                    const float vv[2] = {cv.x, cv.y};
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int kl = k0 + h - KS * hl;
+                        if (kl >= 0 && kl < K) dbg.res[((drow * K + kl) * 2 + part) * NMOD32 + k] = (uint16_t)vv[h];
+                    }
+                }
                 if (k0 < Kout)
                     *reinterpret_cast<uint16_t *>(sStage + stage32_off((uint32_t)k0 * 128 + c, 0) + koff) =
                         (uint16_t)(hv & 0xFFFFu);
@@ -505,10 +530,24 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
 #pragma unroll
                     for (int i = 0; i < 11; i++) asm volatile("" : "+r"(wr[i]), "+r"(wi[i]));
                     if (bi < nb_next) preset(bi);
-                    const float re = crt_pack32(wr, e - 46, M, halfM);
-                    const float im = crt_pack32(wi, e - 46, M, halfM);
+                    int64_t zr = 0, zi = 0, Rr = 0, Ri = 0;
+                    const float re = crt_pack32(wr, e - 46, M, halfM, DBG ? &zr : nullptr, DBG ? &Rr : nullptr);
+                    const float im = crt_pack32(wi, e - 46, M, halfM, DBG ? &zi : nullptr, DBG ? &Ri : nullptr);
                     const int kl = kout_of(b0, bi) - KS * hl;  // output index within this thread's line
                     if (cvalid && kl < K) out[obase + (int64_t)kl * ostride] = make_float2(re, im);
+                    if (DBG && drow >= 0 && kl < K) {
+                        const int64_t o = drow * K + kl;
+#pragma unroll
+                        for (int i = 0; i < 11; i++) {
+                            dbg.acc[(o * 2 + 0) * 11 + i] = wr[i];
+                            dbg.acc[(o * 2 + 1) * 11 + i] = wi[i];
+                        }
+                        dbg.zhat[o * 2] = zr;
+                        dbg.zhat[o * 2 + 1] = zi;
+                        const uint32_t sr = (uint32_t)(Rr >> 63), si = (uint32_t)(Ri >> 63);
+                        dbg.put_R128(drow, kl, 0, (uint32_t)Rr, (uint32_t)((uint64_t)Rr >> 32), sr, sr);
+                        dbg.put_R128(drow, kl, 1, (uint32_t)Ri, (uint32_t)((uint64_t)Ri >> 32), si, si);
+                    }
                 }
             }
             tmem_wait_st();
@@ -549,8 +588,20 @@ size_t fp32_smem_bytes(int Kout, int npad) {
     return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * 8 * (size_t)npad * npad * 2 + PA32_N * 32;
 }
 
+template <int LPV, bool DBG>
+static cudaError_t launch32(int smem, unsigned blocks, cudaStream_t s, const uint8_t *planes, const void *pab,
+                            const ColMapT &map, int64_t ncols, int K, int kslots, const float2 *in, float2 *out,
+                            int *status, int nsm, int tma_in, const DebugDump &dbg) {
+    cudaError_t err =
+        cudaFuncSetAttribute(stage_fp32_kernel<32, LPV, DBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    stage_fp32_kernel<32, LPV, DBG><<<blocks, F32_WARPS * 32, smem, s>>>(planes, (const uint8_t *)pab, map, ncols, K,
+                                                                        kslots, in, out, status, nsm, tma_in, dbg);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stage_fp32(const AxisTables &t, const void *pab, int *status, const StageGeom &g, int stage,
-                              const float2 *in, float2 *out, cudaStream_t s) {
+                              const float2 *in, float2 *out, cudaStream_t s, const DebugDump *dbg) {
     const int K = stage == 1 ? g.q : g.p;
     if (K > 32) return cudaErrorInvalidValue;
     int dev = 0, nsm = 0;
@@ -590,23 +641,21 @@ cudaError_t launch_stage_fp32(const AxisTables &t, const void *pab, int *status,
     // TMA bulk copies of the input need 16-byte aligned starts and sizes: an
     // even line length (stage 1), even n and K (stage 2), aligned base
     const int tma_in = ((uintptr_t)in % 16 == 0) && (g.n % 2 == 0) && (stage == 1 || K % 2 == 0);
-    if (lpv == 4) {
-        err = cudaFuncSetAttribute(stage_fp32_kernel<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        stage_fp32_kernel<32, 4><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, map, ncols, K, kslots, in, out, status, nsm, tma_in);
-    } else if (lpv == 2) {
-        err = cudaFuncSetAttribute(stage_fp32_kernel<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        stage_fp32_kernel<32, 2><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, map, ncols, K, kslots, in, out, status, nsm, tma_in);
-    } else {
-        err = cudaFuncSetAttribute(stage_fp32_kernel<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        stage_fp32_kernel<32, 1><<<(unsigned)blocks, F32_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, map, ncols, K, kslots, in, out, status, nsm, tma_in);
+    DebugDump d;
+    if (dbg) {
+        d = *dbg;
+        d.Lpad = map.Lpad;
     }
-    return cudaGetLastError();
+    const unsigned nb = (unsigned)blocks;
+    const int sm = (int)smem;
+    if (dbg) {
+        if (lpv == 4) return launch32<4, true>(sm, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, tma_in, d);
+        if (lpv == 2) return launch32<2, true>(sm, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, tma_in, d);
+        return launch32<1, true>(sm, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, tma_in, d);
+    }
+    if (lpv == 4) return launch32<4, false>(sm, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, tma_in, d);
+    if (lpv == 2) return launch32<2, false>(sm, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, tma_in, d);
+    return launch32<1, false>(sm, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, tma_in, d);
 }
 
 }  // namespace obfft

@@ -68,6 +68,8 @@ static_assert(fp8_plane_offset(NMOD) == FP8_PLANES_PER_GROUP, "plane table size"
 constexpr int FP8_BPLANES = 12;  // planes of one modulus' constant operand buffer (at most 4 x 3)
 
 constexpr int PA_N = 48;          // Phase A output columns (Re 24 | Im 24)
+constexpr int PA_GSLOTS = 2;      // Phase-A accumulator slots per quarter-warp group (8 x 48 TMEM columns)
+constexpr int PA_SLOTS = 4 * PA_GSLOTS;
 constexpr int PA_ROWB = 384;      // bytes per 8-row group of the staging (3 K-chunks)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
@@ -257,41 +259,53 @@ __device__ __forceinline__ void combine_classes(const uint32_t (&r)[5][OPT], con
 }
 
 // Epilogue of modulus k for this thread's OPT outputs of the Re and Im
-// products: offset residues as FP16 into the Phase-A staging.  The loads of
-// the Im classes are in flight while the Re residues are reduced and stored.
+// products: offset residues as FP16 into the Phase-A staging, where the Re
+// and Im residues of modulus k are neighbours along K (columns 2k and 2k + 1
+// of the output's row), so each output takes one 32-bit store.  The loads of
+// the Im classes are in flight while the Re residues are reduced.
+// dres (debug instantiations only): the dump row of this thread's column,
+// receiving the offset residues of its outputs kl = slot - kbase < Kline.
 template <int KIND, int OPT>
 __device__ __forceinline__ void epilogue_modulus(uint32_t tacc_re, uint32_t tacc_im, int npad, const ModConsts &mc,
-                                                 int k, uint8_t *sStage, int c, int qd, int Kout) {
+                                                 int k, uint8_t *sStage, int c, int qd, int Kout,
+                                                 uint16_t *dres = nullptr, int kbase = 0, int Kline = 0) {
     const float2 nm2 = f2splat(-mc.fm[k]), im2 = f2splat(mc.finv[k]);
     uint32_t r[5][OPT];
-    float2 res[OPT / 2];
+    float2 res[OPT / 2], cvR[OPT / 2];
     load_classes<KIND, OPT>(tacc_re, npad, r);
     tmem_wait_ld();
     regs_after_wait<KIND, OPT>(r);
     combine_classes<KIND, OPT>(r, mc, k, res);
     zero_high_classes<KIND, OPT>(tacc_re, npad);
+    load_classes<KIND, OPT>(tacc_im, npad, r);
 #pragma unroll
-    for (int part = 0; part < 2; part++) {
-        if (part == 0) load_classes<KIND, OPT>(tacc_im, npad, r);
-        const int kk = part == 0 ? k : 12 + k;  // staging column: Re residues, then Im
-        const uint32_t koff = (uint32_t)(kk >> 3) * 128 + (uint32_t)(kk & 7) * 2;
+    for (int o2 = 0; o2 < OPT / 2; o2++) cvR[o2] = offset_residue2(res[o2], nm2, im2);
+    tmem_wait_ld();
+    regs_after_wait<KIND, OPT>(r);
+    combine_classes<KIND, OPT>(r, mc, k, res);
+    zero_high_classes<KIND, OPT>(tacc_im, npad);
+    // column 2k of the staging row (K-major: 8 FP16 per 16-byte core row)
+    uint8_t *base = sStage + stage_off((uint32_t)(qd * OPT) * 128 + c, 0) + (uint32_t)(k >> 2) * 128 +
+                    (uint32_t)(k & 3) * 4;
 #pragma unroll
-        for (int o2 = 0; o2 < OPT / 2; o2++) {
-            const float2 cv = offset_residue2(res[o2], nm2, im2);
-            const uint32_t hv = f16x2(cv.x, cv.y);  // exact: offset residues in [2, 2046]
-            const int k0 = qd * OPT + 2 * o2;
-            if (k0 < Kout)
-                *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)k0 * 128 + c, 0) + koff) =
-                    (uint16_t)(hv & 0xFFFFu);
-            if (k0 + 1 < Kout)
-                *reinterpret_cast<uint16_t *>(sStage + stage_off((uint32_t)(k0 + 1) * 128 + c, 0) + koff) =
-                    (uint16_t)(hv >> 16);
-        }
-        if (part == 0) {
-            tmem_wait_ld();
-            regs_after_wait<KIND, OPT>(r);
-            combine_classes<KIND, OPT>(r, mc, k, res);
-            zero_high_classes<KIND, OPT>(tacc_im, npad);
+    for (int o2 = 0; o2 < OPT / 2; o2++) {
+        const float2 cvI = offset_residue2(res[o2], nm2, im2);
+        // exact: offset residues in [2, 2046]
+        const uint32_t w0 = f16x2(cvR[o2].x, cvI.x), w1 = f16x2(cvR[o2].y, cvI.y);
+        const int k0 = qd * OPT + 2 * o2;
+        // each output slot is 128 staging rows = 16 row groups further on
+        if (k0 < Kout) *reinterpret_cast<uint32_t *>(base + (uint32_t)(2 * o2) * (16 * PA_ROWB)) = w0;
+        if (k0 + 1 < Kout) *reinterpret_cast<uint32_t *>(base + (uint32_t)(2 * o2 + 1) * (16 * PA_ROWB)) = w1;
+        if (dres) {
+            const float vr[2] = {cvR[o2].x, cvR[o2].y}, vi[2] = {cvI.x, cvI.y};
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int kl = k0 + h - kbase;
+                if (kl >= 0 && kl < Kline) {
+                    dres[(kl * 2 + 0) * NMOD + k] = (uint16_t)vr[h];
+                    dres[(kl * 2 + 1) * NMOD + k] = (uint16_t)vi[h];
+                }
+            }
         }
     }
 }
@@ -387,11 +401,15 @@ struct CarrierCfg {
 // KS h).  The threads of quarter-warp group qd work on line qd / (4 / LPV),
 // so every thread still deconstructs, reduces and finishes elements of one
 // line only; a CTA covers 128 LPV lines.
-template <int NPAD, int CAR, int LPV>
+// DBG: also write the stage's integers of the dumped columns to `dbg` (the
+// column exponent, x~, the offset residues, the Phase-A accumulators, zhat and
+// the centred R); the transform itself is unchanged.
+template <int NPAD, int CAR, int LPV, bool DBG>
 __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     stage_fp8_kernel(const uint8_t *__restrict__ planes, const uint8_t *__restrict__ pab,
                      const ModConsts *__restrict__ gmc, ColMapT map, int64_t ncols, int K, int Kout,
-                     const double2 *__restrict__ in, double2 *__restrict__ out, int *status, int pf_ahead) {
+                     const double2 *__restrict__ in, double2 *__restrict__ out, int *status, int pf_ahead,
+                     DebugDump dbg) {
     using CF = Fp8Cfg<NPAD>;
     using CC = CarrierCfg<NPAD, CAR>;
     constexpr int EPT = CF::EPT, OPT = CF::OPT, WPP = CF::WPP;
@@ -399,8 +417,12 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     extern __shared__ __align__(1024) uint8_t smem[];
     const ModConsts &mc = c_fp8_mc;
     __shared__ int colpart[4][128];
-    // 0,1: B planes (TMA, per buffer), 2: MMA, 4: Phase-A B, 5: input tile
+    // 0,1: B planes (TMA, per buffer), 2 (and 3 in the FP16 carrier): MMA,
+    // 4: Phase-A B, 5: input tile
     __shared__ __align__(8) uint64_t mbar[6];
+    // Phase-A accumulator slots: MMAs complete (one commit) / slot read and
+    // preset again (one arrival per warp of the owning quarter-warp group)
+    __shared__ __align__(8) uint64_t pa_full[PA_SLOTS], pa_empty[PA_SLOTS];
     __shared__ uint32_t tmem_holder;
     // FP16 carrier pipeline: failure flags of the steps, read by every thread
     // right after the barrier that starts step t from slot t & 1; failures are
@@ -451,6 +473,10 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             if (CAR) fail[0] = fail[1] = 0;
             s_e0 = itile.e0;
             for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
+            for (int b = 0; b < PA_SLOTS; b++) {
+                mbar_init(smem_u32(&pa_full[b]), 1);
+                mbar_init(smem_u32(&pa_empty[b]), 4);
+            }
             mbar_fence_init();
         }
         __syncwarp();
@@ -526,6 +552,22 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             pI[jj] = scale_split(xb[jj][1], e);
         }
     }
+    const int64_t drow = DBG && cvalid ? dbg.row(cg) : -1;
+    if (DBG && drow >= 0) {
+        if (qd == QPL * hl) dbg.e[drow] = e;
+        auto xt_of = [](const Pieces &pc) {
+            return (int64_t)(((uint64_t)pc.p2 << 40) | ((uint64_t)pc.p1 << 20) | (uint64_t)pc.p0) - (1ll << 55);
+        };
+#pragma unroll
+        for (int jj = 0; jj < EPT; jj++) {
+            const int j = EPT * qd + jj - KS * hl;
+            if (j < K) {
+                dbg.xt[(drow * K + j) * 2] = xt_of(pR[jj]);
+                dbg.xt[(drow * K + j) * 2 + 1] = xt_of(pI[jj]);
+            }
+        }
+    }
+    uint16_t *const dres = DBG && drow >= 0 ? dbg.res + drow * (int64_t)K * 2 * NMOD : nullptr;
 
     // digits of x_R and x_I for modulus k into A buffer (k & 1)
     auto gen = [&](int k) {
@@ -632,7 +674,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         prefetch_b(1);  // buffer 1 is unused so far
     }
     uint32_t mph[1] = {0u};  // next phase parity of the MMA barrier mbar[2]
-    uint32_t mph3 = 0u;      // next phase parity of mbar[3]
     int last_issued = 0, last_waited = -1;  // FP16 carrier, thread 0: MMA batches in flight
     if constexpr (CAR) {
         // FP16 carrier: two accumulator sets.  The MMAs of modulus k+1 (set
@@ -671,10 +712,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 }
             }
             const uint32_t tre = tmem + lanebase + (uint32_t)(k & 1) * F16_ACC + (uint32_t)(qd * OPT);
-            epilogue_modulus<KIND_F16, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+            epilogue_modulus<KIND_F16, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout, dres, KS * hl, K);
         }
-        mph[0] = (uint32_t)(((NSTEP + 1) / 2) & 1);
-        mph3 = (uint32_t)((NSTEP / 2) & 1);
     } else {
         // A failure (an MMA wait or, in thread 0, issue() giving up) stays in
         // the thread's own tfail and reaches the CTA through the next
@@ -689,11 +728,11 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 const uint32_t tre = tmem + lanebase + (uint32_t)(qd * OPT);
                 const int kind = fp8_kind(k);
                 if (kind == KIND_SQ)
-                    epilogue_modulus<KIND_SQ, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+                    epilogue_modulus<KIND_SQ, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout, dres, KS * hl, K);
                 else if (kind == KIND_B9)
-                    epilogue_modulus<KIND_B9, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+                    epilogue_modulus<KIND_B9, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout, dres, KS * hl, K);
                 else
-                    epilogue_modulus<KIND_B11, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout);
+                    epilogue_modulus<KIND_B11, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout, dres, KS * hl, K);
             } else {
                 tfail = true;
             }
@@ -716,38 +755,70 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     }
 
     // ---------------- CRT Phase A on FP16 tensor cores, then Kulisch + lift + pack ----
-    // Waves of per_wave row blocks (one block = one output k for the 128
-    // columns, N = 48 accumulators).  Accumulators start at 2^23 (the FP32 bit
-    // pattern of 2^23 + P is 0x4B000000 + P); each thread presets the next
-    // wave's columns right after reading them, so one CTA barrier per wave
-    // orders both the reads and the presets before the next wave's MMAs.
-    bool pend3 = false;   // a commit to mbar[3] is in flight (thread 0's view)
+    // Row block b (one output slot for the 128 columns, N = 48 accumulators)
+    // belongs to quarter-warp group g = b & 3 (its four warps cover the 128
+    // TMEM lanes), which owns PA_GSLOTS accumulator slots of 48 columns: its
+    // i-th block b = g + 4 i accumulates in slot PA_GSLOTS g + i % PA_GSLOTS.
+    // Accumulators start at 2^23 (the FP32 bit pattern of 2^23 + P is
+    // 0x4B000000 + P).  After its four warps have read block b and preset the
+    // slot again (the slot's empty barrier), the group's first warp issues the
+    // MMAs of block b + 4 PA_GSLOTS into it; they run while the group finishes
+    // block b.  No CTA barrier separates the blocks, and the groups never wait
+    // for one another.
+    const int nblk = Kout;
+    const bool leader = sub == 0 && lane == 0;  // issues the MMAs of its group's blocks
+    int pa_last = -1;                            // leader: last block whose MMAs it issued
+    auto gslot = [&](int b) { return PA_GSLOTS * (b & 3) + ((b >> 2) % PA_GSLOTS); };
+    auto preset = [&](int b) {
+        const uint32_t ta = tmem + lanebase + (uint32_t)(gslot(b) * PA_N);
+        tmem_st16_const(ta, 0x4B000000u);
+        tmem_st16_const(ta + 16, 0x4B000000u);
+        tmem_st16_const(ta + 32, 0x4B000000u);
+    };
     if (ok) {
-        const int per_wave = Kout % 8 == 0 ? 8 : 10;  // 8: two row blocks per quarter-warp per wave
-        auto preset = [&](int bi) {
-            const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
-            tmem_st16_const(ta, 0x4B000000u);
-            tmem_st16_const(ta + 16, 0x4B000000u);
-            tmem_st16_const(ta + 32, 0x4B000000u);
-        };
-        for (int bi = qd; bi < min(per_wave, Kout); bi += 4) preset(bi);
+        for (int i = 0; i < PA_GSLOTS && qd + 4 * i < nblk; i++) preset(qd + 4 * i);
         tmem_wait_st();
         tc_fence_before();
         fence_async_smem();
         const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
         ok = __syncthreads_or(bad | (int)(tfail && !CAR)) == 0;  // uniform decision across the CTA
         if (CAR && fail[NSTEP & 1]) ok = false;  // a failed wait in the last pipeline step
+    }
+    if (ok) {
         const uint32_t idescA = instr_desc(128, PA_N, 0);
         const uint64_t adescA = smem_desc(smem_u32(sStage), 128, PA_ROWB);
         const uint64_t bdescA0 = smem_desc(smem_u32(sPAB), 128, 512), bdescA1 = smem_desc(smem_u32(sPAB) + 256, 128, 512);
         const uint32_t ebias[4] = {mc.kbias[0], mc.kbias[1], mc.kbias[2], mc.kbias[3]};
         const uint64_t zbias = ((uint64_t)mc.zbias[1] << 32) | mc.zbias[0];
+        // output slot of row block b.  With LPV lines per lane, block b
+        // belongs to line (b & 3) / QPL, so the thread that finishes the
+        // blocks b = qd (mod 4) stays on its own line; every 8 consecutive
+        // blocks cover 8 / LPV consecutive outputs of every line (LPV = 2:
+        // blocks 0, 1, 4, 5 are outputs 0 .. 3 of line 0)
+        auto kout_of = [&](int b) -> int {
+            const int b0 = b & ~7, bi = b & 7;
+            if constexpr (LPV == 1) return b;
+            else if constexpr (LPV == 2) return KS * ((bi & 3) >> 1) + (b0 >> 1) + 2 * (bi >> 2) + (bi & 1);
+            else return KS * (bi & 3) + (b0 >> 2) + (bi >> 2);
+        };
+        // the two K-chunk MMAs of block b into its slot, committed to the slot's full barrier
+        auto issue_block = [&](int b) {
+            tc_fence_after();
+            // a row block's descriptor lies 16 x PA_ROWB bytes (in 16-byte
+            // units) per output slot past the staging start
+            const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b) * (16 * PA_ROWB / 16));
+            const uint32_t d = tmem + (uint32_t)(gslot(b) * PA_N);
+            tc_mma_f16(d, ad, bdescA0, idescA, 1);
+            tc_mma_f16(d, ad + 16, bdescA1, idescA, 1);  // + 256 bytes: K 16..31
+            tc_commit(smem_u32(&pa_full[gslot(b)]));
+            pa_last = b;
+        };
         // the 42 used accumulator words of a row block: Re 0..20, Im 24..44
-        auto load_block = [&](int bi, uint32_t (&wv)[42]) {
-            const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA_N);
-            uint32_t a[16], b[4], c16[16], d[4];
+        auto load_block = [&](int b, uint32_t (&wv)[42]) {
+            const uint32_t ta = tmem + lanebase + (uint32_t)(gslot(b) * PA_N);
+            uint32_t a[16], bb[4], c16[16], d[4];
             tmem_ld16(ta, a);
-            tmem_ld4(ta + 16, b);
+            tmem_ld4(ta + 16, bb);
             tmem_ld1(ta + 20, wv[20]);
             tmem_ld16(ta + 24, c16);
             tmem_ld4(ta + 40, d);
@@ -759,7 +830,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             }
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                wv[16 + i] = b[i];
+                wv[16 + i] = bb[i];
                 wv[37 + i] = d[i];
             }
         };
@@ -769,68 +840,63 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         };
         auto finish = [&](const uint32_t (&wv)[42], int kout) {
             bool slow_re, slow_im, near_re, near_im;
-            uint32_t Rre[4], Rim[4];
-            double re = kulisch_pack_fp8_fast(wv, mc, e - 104, ebias, zbias, slow_re, Rre, near_re);
-            double im = kulisch_pack_fp8_fast(wv + 21, mc, e - 104, ebias, zbias, slow_im, Rim, near_im);
+            uint32_t Rre[4], Rim[4], zre = 0, zim = 0;
+            double re = kulisch_pack_fp8_fast(wv, mc, e - 104, ebias, zbias, slow_re, Rre, near_re, DBG ? &zre : nullptr);
+            double im = kulisch_pack_fp8_fast(wv + 21, mc, e - 104, ebias, zbias, slow_im, Rim, near_im,
+                                              DBG ? &zim : nullptr);
             if (slow_re) re = kulisch_finish_slow(Rre[0], Rre[1], Rre[2], Rre[3], near_re, e - 104);
             if (slow_im) im = kulisch_finish_slow(Rim[0], Rim[1], Rim[2], Rim[3], near_im, e - 104);
             const int kl = kout - KS * hl;  // the output index within this thread's line
             if (cvalid && kl < (LPV == 1 ? Kout : K)) out[obase + (int64_t)kl * ostride] = make_double2(re, im);
-        };
-        // output slot of row block bi of the wave starting at b0.  With LPV
-        // lines per lane, block bi belongs to line (bi & 3) / QPL, so the
-        // thread that finishes blocks qd and qd + 4 stays on its own line;
-        // each wave covers 8 / LPV consecutive outputs of every line (LPV = 2:
-        // blocks 0, 1, 4, 5 are outputs 4w .. 4w + 3 of line 0)
-        auto kout_of = [&](int b0, int bi) -> int {
-            if constexpr (LPV == 1) return b0 + bi;
-            else if constexpr (LPV == 2) return KS * ((bi & 3) >> 1) + (b0 >> 1) + 2 * (bi >> 2) + (bi & 1);
-            else return KS * (bi & 3) + (b0 >> 2) + (bi >> 2);
-        };
-        for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
-            const int nb = min(per_wave, Kout - b0);
-            const int nb_next = min(per_wave, Kout - b0 - per_wave);  // <= 0: no next wave
-            // two commits per wave: row blocks 0..3 on mbar[2], the rest (possibly
-            // none) on mbar[3], so the second group's MMAs run while the first
-            // group is finished; every thread waits once on each barrier per wave
-            if (tid == 0) {
-                tc_fence_after();
-                // a row block's descriptor lies 16 x PA_ROWB bytes (in 16-byte
-                // units) per output slot past the staging start
-                uint32_t d = tmem;
-                const int na = min(nb, 4);
-                for (int bi = 0; bi < nb; bi++) {
-                    const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b0, bi) * (16 * PA_ROWB / 16));
-                    tc_mma_f16(d, ad, bdescA0, idescA, 1);
-                    tc_mma_f16(d, ad + 16, bdescA1, idescA, 1);  // + 256 bytes: K 16..31
-                    d += PA_N;
-                    if (bi == na - 1) tc_commit(smem_u32(&mbar[2]));
+            if (DBG && drow >= 0 && kl < K) {
+                const int64_t o = drow * K + kl;
+#pragma unroll
+                for (int i = 0; i < 21; i++) {
+                    dbg.acc[(o * 2 + 0) * 21 + i] = wv[i];
+                    dbg.acc[(o * 2 + 1) * 21 + i] = wv[21 + i];
                 }
-                tc_commit(smem_u32(&mbar[3]));
-                pend3 = true;
+                dbg.zhat[o * 2] = zre;
+                dbg.zhat[o * 2 + 1] = zim;
+                const uint32_t *Rw[2] = {Rre, Rim};
+                const bool nr[2] = {near_re, near_im};
+#pragma unroll
+                for (int part = 0; part < 2; part++) {
+                    // the centred value: the two-sided correction where the lift was near a boundary
+                    const u128 r = (u128)lift_centre(Rw[part], nr[part], mc);
+                    dbg.put_R128(drow, kl, part, (uint32_t)r, (uint32_t)(r >> 32), (uint32_t)(r >> 64), (uint32_t)(r >> 96));
+                }
             }
-            auto do_block = [&](int bi) {
-                uint32_t wv[42];
-                load_block(bi, wv);
-                tmem_wait_ld();
-                after_wait(wv);
-                if (bi < nb_next) preset(bi);
-                finish(wv, kout_of(b0, bi));
-            };
-            const bool okA = mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
-            mph[0] ^= 1u;
+        };
+        if (leader)
+            for (int i = 0; i < PA_GSLOTS && qd + 4 * i < nblk; i++) issue_block(qd + 4 * i);
+        for (int i = 0, b = qd; b < nblk; i++, b += 4) {
+            const int sl = gslot(b);
+            const uint32_t use = (uint32_t)((i / PA_GSLOTS) & 1);  // phase parity of this use of the slot
+            const bool okb = mbar_wait(smem_u32(&pa_full[sl]), use, WAIT_LIMIT);
             tc_fence_after();
-            if (okA && qd < nb) do_block(qd);
-            const bool okB = mbar_wait(smem_u32(&mbar[3]), mph3, WAIT_LIMIT);
-            mph3 ^= 1u;
-            pend3 = false;
-            tc_fence_after();
-            if (okA && okB)
-                for (int bi = qd + 4; bi < nb; bi += 4) do_block(bi);
-            tmem_wait_st();
-            tc_fence_before();
-            if (__syncthreads_or(!(okA && okB))) ok = false;
+            uint32_t wv[42];
+            load_block(b, wv);
+            tmem_wait_ld();
+            after_wait(wv);
+            const int bn = b + 4 * PA_GSLOTS;  // the group's next block in this slot
+            if (bn < nblk) {
+                preset(bn);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&pa_empty[sl]));
+                if (leader) {
+                    if (mbar_wait(smem_u32(&pa_empty[sl]), use, WAIT_LIMIT)) issue_block(bn);
+                    else tfail = true;
+                }
+            }
+            if (!okb) {
+                tfail = true;
+                continue;
+            }
+            finish(wv, kout_of(b));
         }
+        ok = __syncthreads_or((int)tfail) == 0;
     }
     if (!ok && tid == 0) {
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
@@ -841,11 +907,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             for (int j = last_waited + 1; j <= last_issued; j++)
                 mbar_wait(smem_u32(&mbar[2 + (j & 1)]), (uint32_t)((j >> 1) & 1), WAIT_LIMIT);
         }
-        mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
-        if (pend3) mbar_wait(smem_u32(&mbar[3]), mph3, WAIT_LIMIT);
+        if (!CAR) mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
         mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
         mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT);
     }
+    // Phase A on the failure path: each leader's last commit completes once
+    // every MMA it issued has (the waits are bounded)
+    if (!ok && leader && pa_last >= 0)
+        mbar_wait(smem_u32(&pa_full[gslot(pa_last)]), (uint32_t)(((pa_last >> 2) / PA_GSLOTS) & 1), WAIT_LIMIT);
     tc_fence_before();
     __syncthreads();
     if (w == 0) tmem_dealloc(tmem, 512);
@@ -885,9 +954,22 @@ static size_t fp16_smem_bytes(int Kout, int npad) {
     return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * 8 * (size_t)npad * npad * 2;
 }
 
+template <int CAR, int LPV, bool DBG>
+static cudaError_t launch_one(int smem, unsigned blocks, cudaStream_t s, const uint8_t *planes, const void *pab,
+                              const ColMapT &map, int64_t ncols, int K, int kslots, const double2 *in, double2 *out,
+                              int *status, int nsm, const DebugDump &dbg) {
+    cudaError_t err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, LPV, DBG>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    stage_fp8_kernel<32, CAR, LPV, DBG><<<blocks, FP8_WARPS * 32, smem, s>>>(
+        planes, (const uint8_t *)pab, nullptr, map, ncols, K, kslots, in, out, status, nsm, dbg);
+    return cudaGetLastError();
+}
+
 template <int CAR>
 static cudaError_t launch_stage_carrier(const AxisTables &t, const void *pab, int *status, const StageGeom &g,
-                                        int stage, const double2 *in, double2 *out, cudaStream_t s) {
+                                        int stage, const double2 *in, double2 *out, cudaStream_t s,
+                                        const DebugDump *dbg) {
     const int K = stage == 1 ? g.q : g.p;
     if (K > 32) return cudaErrorInvalidValue;
     int dev = 0, nsm = 0;
@@ -929,35 +1011,34 @@ static cudaError_t launch_stage_carrier(const AxisTables &t, const void *pab, in
     const size_t smem = CAR ? fp16_smem_bytes(kslots, 32) : fp8_smem_bytes(kslots, 32);
     int64_t blocks = (ncols + tile - 1) / tile;
     if (blocks == 0) return cudaSuccess;
-    if (lpv == 4) {
-        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        stage_fp8_kernel<32, CAR, 4><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, nullptr, map, ncols, K, kslots, in, out, status, nsm);
-    } else if (lpv == 2) {
-        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        stage_fp8_kernel<32, CAR, 2><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, nullptr, map, ncols, K, kslots, in, out, status, nsm);
-    } else {
-        err = cudaFuncSetAttribute(stage_fp8_kernel<32, CAR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        stage_fp8_kernel<32, CAR, 1><<<(unsigned)blocks, FP8_WARPS * 32, smem, s>>>(
-            planes, (const uint8_t *)pab, nullptr, map, ncols, K, kslots, in, out, status, nsm);
+    DebugDump d;
+    if (dbg) {
+        d = *dbg;
+        d.Lpad = map.Lpad;
     }
-    return cudaGetLastError();
+    const unsigned nb = (unsigned)blocks;
+    if (dbg) {
+        if (lpv == 4) return launch_one<CAR, 4, true>((int)smem, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, d);
+        if (lpv == 2) return launch_one<CAR, 2, true>((int)smem, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, d);
+        return launch_one<CAR, 1, true>((int)smem, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, d);
+    }
+    if (lpv == 4) return launch_one<CAR, 4, false>((int)smem, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, d);
+    if (lpv == 2) return launch_one<CAR, 2, false>((int)smem, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, d);
+    return launch_one<CAR, 1, false>((int)smem, nb, s, planes, pab, map, ncols, K, kslots, in, out, status, nsm, d);
 }
 
 cudaError_t launch_stage_fp8(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
-                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s) {
+                             const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s,
+                             const DebugDump *dbg) {
     (void)dmc;
-    return launch_stage_carrier<0>(t, pab, status, g, stage, in, out, s);
+    return launch_stage_carrier<0>(t, pab, status, g, stage, in, out, s, dbg);
 }
 
 cudaError_t launch_stage_fp16(const AxisTables &t, const ModConsts *dmc, const void *pab, int *status,
-                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s) {
+                              const StageGeom &g, int stage, const double2 *in, double2 *out, cudaStream_t s,
+                              const DebugDump *dbg) {
     (void)dmc;
-    return launch_stage_carrier<1>(t, pab, status, g, stage, in, out, s);
+    return launch_stage_carrier<1>(t, pab, status, g, stage, in, out, s, dbg);
 }
 
 }  // namespace obfft

@@ -68,13 +68,15 @@ struct ColMap {
 // block (k slots 0..15: G b0, 16..31: H b1), so each residue product is one
 // limb GEMM block instead of two half-empty ones: [gi][mod][prod][lane] uint2
 // holding (b0 word, b1 word).
-template <int KPAD, int MT>
+// DBG: also write the stage's integers (column exponent, x~, D/E/F, the
+// canonical residues v, zhat and R) of the dumped columns to `dbg`.
+template <int KPAD, int MT, bool DBG>
 __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__restrict__ table,
                                                               const ModConsts *__restrict__ gmc,
                                                               ColMap map, int64_t ncols, int K,
                                                               int Kout,
                                                               const double2 *__restrict__ in,
-                                                              double2 *__restrict__ out) {
+                                                              double2 *__restrict__ out, DebugDump dbg) {
     constexpr bool PK = KPAD == 16;         // b0 and b1 limbs in one k32 block
     constexpr int KB = PK ? 1 : KPAD / 32;  // k32 blocks of data elements
     constexpr int KB2 = PK ? 1 : 2 * KB;    // limb GEMM blocks (b0 limbs then b1 limbs)
@@ -117,6 +119,8 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
     lead = max(lead, __shfl_xor_sync(0xffffffffu, lead, 2));
     const int e = lead == LEAD_ZERO ? 0 : lead;
     if (sub == 0 && tig == 0) colexp[col_local] = e;
+    const int64_t drow = DBG && cvalid ? dbg.row(c) : -1;
+    if (DBG && drow >= 0 && sub == 0 && tig == 0) dbg.e[drow] = e;
     __syncthreads();  // mc ready
 
 #pragma unroll
@@ -128,6 +132,13 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
             for (int i = 0; i < 4; i++) {
                 int64_t a = scale_round(xb[kb][h][i][0], e);
                 int64_t b = scale_round(xb[kb][h][i][1], e);
+                if (DBG && drow >= 0 && sub == 0) {
+                    const int j = kb * 32 + h * 16 + 4 * tig + i;
+                    if (j < K) {
+                        dbg.xt[(drow * K + j) * 2] = a;
+                        dbg.xt[(drow * K + j) * 2 + 1] = b;
+                    }
+                }
                 pr[h][i] = split_pieces(a);
                 pi[h][i] = split_pieces(b);
             }
@@ -213,6 +224,19 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
             int32_t D = T[0][i], Ev = T[1][i], Fv = T[2][i];
             uint32_t vr = mod_signed27(D - Ev, m, mu, off);       // Re = D - E
             uint32_t vi = mod_signed27(Fv - D - Ev, m, mu, off);  // Im = F - D - E
+            if constexpr (DBG) {
+                const int kout = mt * 16 + grp + ((i >> 1) << 3);
+                const int64_t cc = c0 + gi * 8 + 2 * tig + (i & 1);
+                const int64_t d = map.valid(cc, ncols) ? dbg.row(cc) : -1;
+                if (d >= 0 && kout < Kout) {
+                    uint16_t *pd = dbg.def + ((d * Kout + kout) * NMOD + k) * 3;
+                    pd[0] = (uint16_t)mod_signed27(D, m, mu, off);
+                    pd[1] = (uint16_t)mod_signed27(Ev, m, mu, off);
+                    pd[2] = (uint16_t)mod_signed27(Fv, m, mu, off);
+                    dbg.res[((d * Kout + kout) * 2 + 0) * NMOD + k] = (uint16_t)vr;
+                    dbg.res[((d * Kout + kout) * 2 + 1) * NMOD + k] = (uint16_t)vi;
+                }
+            }
             uint32_t vv[2] = {vr, vi};
 #pragma unroll
             for (int part = 0; part < 2; part++) {
@@ -243,6 +267,15 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
             int64_t zhat = (int64_t)__float2int_rn(zf[o]);
             i128 R = lift_two_sided(E, zhat, mc);
             res[part] = pack_rne(R, colexp[cl] - 104);
+            if constexpr (DBG) {
+                const int64_t d = dbg.row(cc);
+                if (d >= 0) {
+                    dbg.zhat[(d * Kout + kout) * 2 + part] = zhat;
+                    const u128 ur = (u128)R;
+                    dbg.put_R128(d, kout, part, (uint32_t)ur, (uint32_t)(ur >> 32), (uint32_t)(ur >> 64),
+                                 (uint32_t)(ur >> 96));
+                }
+            }
         }
         out[map.out_index(cc, kout)] = make_double2(res[0], res[1]);
     }
@@ -251,20 +284,27 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
 template <int KPAD, int MT>
 static cudaError_t launch_t(const AxisTables &t, const ModConsts *dmc, const ColMap &map,
                             int64_t ncols, int K, int Kout, const double2 *in, double2 *out,
-                            cudaStream_t s) {
+                            cudaStream_t s, const DebugDump *dbg) {
     const void *table = map.stage == 1 ? t.int8_s1 : t.int8_s2;
     size_t smem = (size_t)4 * NMOD * 3 * (KPAD == 16 ? 1 : (KPAD / 32) * 2) * 32 * sizeof(uint2);
-    auto kern = stage_int8_kernel<KPAD, MT>;
+    auto kern = dbg ? stage_int8_kernel<KPAD, MT, true> : stage_int8_kernel<KPAD, MT, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int64_t blocks = (ncols + CT_COLS - 1) / CT_COLS;
     if (blocks == 0) return cudaSuccess;
-    kern<<<(unsigned)blocks, 128 * MT, smem, s>>>((const uint4 *)table, dmc, map, ncols, K, Kout, in, out);
+    DebugDump d;
+    if (dbg) {
+        d = *dbg;
+        d.stage = map.stage;
+        d.L = map.L;
+        d.Lpad = map.Lpad;
+    }
+    kern<<<(unsigned)blocks, 128 * MT, smem, s>>>((const uint4 *)table, dmc, map, ncols, K, Kout, in, out, d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const StageGeom &g,
-                              int stage, const double2 *in, double2 *out, cudaStream_t s) {
+                              int stage, const double2 *in, double2 *out, cudaStream_t s, const DebugDump *dbg) {
     ColMap map;
     map.stage = stage;
     map.L = g.L;
@@ -278,11 +318,11 @@ cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const S
     int MT = (K + 15) / 16;
     bool wide = K > 32;
     if (!wide) {
-        if (MT == 1) return launch_t<16, 1>(t, dmc, map, ncols, K, K, in, out, s);
-        return launch_t<32, 2>(t, dmc, map, ncols, K, K, in, out, s);
+        if (MT == 1) return launch_t<16, 1>(t, dmc, map, ncols, K, K, in, out, s, dbg);
+        return launch_t<32, 2>(t, dmc, map, ncols, K, K, in, out, s, dbg);
     }
-    if (MT == 3) return launch_t<64, 3>(t, dmc, map, ncols, K, K, in, out, s);
-    return launch_t<64, 4>(t, dmc, map, ncols, K, K, in, out, s);
+    if (MT == 3) return launch_t<64, 3>(t, dmc, map, ncols, K, K, in, out, s, dbg);
+    return launch_t<64, 4>(t, dmc, map, ncols, K, K, in, out, s, dbg);
 }
 
 }  // namespace obfft
