@@ -105,11 +105,26 @@ obfft_status obfft_destroy(obfft_plan p);
 obfft_status obfft_plan_get_splits(obfft_plan p, int grid, int axis, int *p_out, int *q_out);
 
 /*
+ * The choices a plan runs with for one axis of one grid: the Bailey split
+ * n = p * q and, for the tcgen05 stage kernels (OBFFT_MODE_FP8, _FP16,
+ * _FP32), the lines per TMEM lane of the stage-1 and stage-2 launches (1, 2
+ * or 4 lines of up to 32, 16 or 8 elements side by side in each lane; 0 for
+ * the other modes and length-1 axes).  Not part of the paper: multi-grid plans
+ * choose both by timing at creation (see obfft_plan_create_many).
+ */
+obfft_status obfft_plan_get_tuning(obfft_plan p, int grid, int axis, int *p_out, int *q_out, int *lpv_stage1,
+                                   int *lpv_stage2);
+
+/*
  * Plan for `count` independent grids of possibly different sizes
  * (dims[g][0..2]) executed together (the uneven batch).  Same size rules as
- * obfft_plan_create (with OBFFT_AUTOTUNE=1 in the environment the splits of
- * each distinct axis length are chosen by timing).  Grids of identical shape
- * and splits form a group that runs as one batched transform; the plan owns
+ * obfft_plan_create.  Unless OBFFT_AUTOTUNE=0 is set in the environment, the
+ * plan is tuned when it is created (OBFFT_AUTOTUNE=1 tunes one-grid plans
+ * too): the split of each distinct axis length and, for the tcgen05 stage
+ * kernels, the lines per TMEM lane of every stage with K <= 8 are chosen by
+ * timing launches on this GPU (obfft_plan_get_tuning reports them; every
+ * choice gives exact results for its split).  Grids of identical shape and
+ * splits form a group that runs as one batched transform; the plan owns
  * device memory of about the total size of the grids, three times that for
  * grids that share their shape.
  */

@@ -39,7 +39,7 @@ EXPORTS = ("obfft_plan_create", "obfft_exec", "obfft_destroy", "obfft_plan_get_s
            "obfft_exec_fp64_noalloc", "obfft_plan_status", "obfft_selftest_bounded_wait",
            "obfft_exec_host", "obfft_host_twiddle32", "obfft_host_crt_constants32",
            "obfft_ablation_phase_b", "obfft_ablation_residues", "obfft_exec_axes", "obfft_transpose_blocks",
-           "obfft_debug_layout", "obfft_exec_debug")
+           "obfft_debug_layout", "obfft_exec_debug", "obfft_plan_get_tuning")
 
 _lib = None
 
@@ -67,6 +67,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.obfft_exec_stage.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     L.obfft_exec_axes.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     L.obfft_transpose_blocks.argtypes = [vp, vp, i64, i64, i64, vp]
+    L.obfft_plan_get_tuning.argtypes = [vp, i32, i32] + [ctypes.POINTER(i32)] * 4
+    L.obfft_plan_get_tuning.restype = i32
     L.obfft_debug_layout.argtypes = [i32, i32, i32, i64, ctypes.POINTER(i64)]
     L.obfft_debug_layout.restype = i32
     L.obfft_exec_debug.argtypes = [vp, i32, i32, vp, vp, i32, i64, i64, vp, vp]
@@ -151,6 +153,13 @@ def obfft_exec_axes(plan: int, first_axis: int, last_axis: int, in_ptr: int, out
 def obfft_transpose_blocks(src_ptr: int, dst_ptr: int, nblocks: int, rows: int, row_bytes: int,
                            stream: int = 0) -> None:
     check(load().obfft_transpose_blocks(src_ptr, dst_ptr, nblocks, rows, row_bytes, stream))
+
+
+def obfft_plan_get_tuning(plan: int, grid: int, axis: int):
+    """(p, q, lines per TMEM lane of stage 1, of stage 2) the plan runs with."""
+    v = [ctypes.c_int() for _ in range(4)]
+    check(load().obfft_plan_get_tuning(plan, grid, axis, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def obfft_debug_layout(mode: int, K: int, Kout: int, ncols: int):

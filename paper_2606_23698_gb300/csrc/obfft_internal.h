@@ -107,6 +107,7 @@ struct AxisTables {
 struct GridDesc {
     int64_t n[3];
     AxisPlan ax[3];
+    int lpv[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // tuned lines per TMEM lane per axis and stage (0: default)
 };
 
 // Default Bailey split of an axis of length n: q = smallest divisor with
@@ -193,7 +194,13 @@ struct StageGeom {
     int64_t L;       // total lines = batch * P
     int64_t P;       // lines per batch item (A1 * A2)
     int n, p, q;
+    int lpv = 0;     // tcgen05 stage kernels: lines per TMEM lane (0: pick_lpv's default)
 };
+// Lines per TMEM lane of a tcgen05 stage launch (FP8, FP16-carrier and FP32
+// modes): the caller's choice when valid (lpv <= fp8_lines_per_lane(K); two
+// at K <= 8 needs the two-line planes), else fp8_lines_per_lane(K), with four
+// lines only when they need fewer rounds of CTAs than two.
+int pick_lpv(const StageGeom &g, int stage, bool have_l2_planes, int nsm);
 cudaError_t launch_stage_int8(const AxisTables &t, const ModConsts *dmc, const StageGeom &g,
                               int stage, const double2 *in, double2 *out, cudaStream_t s,
                               const DebugDump *dbg = nullptr);

@@ -636,11 +636,22 @@ static void free_tables(obfft_plan P) {
 using namespace obfft;
 
 // ------------------------------------------------------------------ autotune
-// With OBFFT_AUTOTUNE=1 in the environment, plan creation times every Bailey
-// split n = p * q (p, q within the mode's limit) of each distinct axis length on
-// a synthetic batch of lines (stage 1 + stage 2 launches, CUDA events, best of
-// 3 after a warm-up) and keeps the fastest.  Results remain exact for the
-// chosen split; the oracle reads the split back through obfft_plan_get_splits.
+// Multi-grid plans (and, with OBFFT_AUTOTUNE=1 in the environment, every
+// plan; OBFFT_AUTOTUNE=0 turns it off) are tuned at creation:
+//  * the Bailey split n = p * q (p, q within the mode's limit) of each distinct
+//    axis length, timed on a synthetic batch of lines (stage 1 + stage 2
+//    launches, CUDA events, best of 3 after a warm-up);
+//  * for the tcgen05 stage kernels, the lines per TMEM lane of every stage
+//    with K <= 8 (four or two), timed on the launch geometry of each group of
+//    same-shape grids.
+// Results remain exact for the chosen split; the oracle reads the split back
+// through obfft_plan_get_splits, and obfft_plan_get_tuning reports both.
+static bool autotune_enabled(obfft_plan P) {
+    const char *env = getenv("OBFFT_AUTOTUNE");
+    if (env && env[0] == '0') return false;
+    if (env && env[0] == '1') return true;
+    return P->grids.size() > 1;
+}
 // Bytes per complex element of the plan's data: complex128, or complex64 for
 // the FP32-precision modes.
 static size_t elem_bytes(int mode) {
@@ -700,8 +711,7 @@ static float time_split(obfft_plan P, int n, int pp, int qq, void *buf, void *tm
 }
 
 static void autotune_splits(obfft_plan P) {
-    const char *env = getenv("OBFFT_AUTOTUNE");
-    if (!env || env[0] != '1') return;
+    if (!autotune_enabled(P)) return;
     const int kmax = mode_kmax(P->mode);
     std::map<int, std::pair<int, int>> best;
     for (auto &gd : P->grids)
@@ -741,6 +751,8 @@ static void autotune_splits(obfft_plan P) {
             }
         }
 }
+
+static void autotune_lpv(obfft_plan P);
 
 static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
     autotune_splits(P);
@@ -820,6 +832,7 @@ static obfft_status finish_create(obfft_plan P, obfft_plan *out) {
             }
         }
     }
+    autotune_lpv(P);
     *out = P;
     return OBFFT_OK;
 }
@@ -946,9 +959,108 @@ static obfft_status run_stage_geom(obfft_plan P, const AxisPlan &ap, const Stage
     return OBFFT_OK;
 }
 
+// Lines per TMEM lane of every stage with K <= 8 (four or two), timed on the
+// launch geometry of each group of same-shape grids (the whole grid for
+// one-grid plans): three launches per candidate after a warm-up, best of two.
+static void autotune_lpv(obfft_plan P) {
+    if (!autotune_enabled(P)) return;
+    if (P->mode != OBFFT_MODE_FP8 && P->mode != OBFFT_MODE_FP16 && P->mode != OBFFT_MODE_FP32) return;
+    std::vector<std::vector<int>> groups = P->groups;
+    if (groups.empty()) groups.push_back({0});
+    const size_t eb = elem_bytes(P->mode);
+    cudaEvent_t ea, eb2;
+    if (cudaEventCreate(&ea) != cudaSuccess) return;
+    if (cudaEventCreate(&eb2) != cudaSuccess) {
+        cudaEventDestroy(ea);
+        return;
+    }
+    for (const auto &grp : groups) {
+        const GridDesc &gd = P->grids[grp[0]];
+        const int64_t batch = P->groups.empty() ? P->batch : (int64_t)grp.size();
+        bool any = false;
+        for (int a = 0; a < 3; a++) any = any || (gd.ax[a].n > 1 && (gd.ax[a].p <= 8 || gd.ax[a].q <= 8));
+        if (!any) continue;
+        const size_t bytes = (size_t)(gd.n[0] * gd.n[1] * gd.n[2] * batch) * eb;
+        void *a = nullptr, *b = nullptr;
+        if (cudaMalloc(&a, bytes) != cudaSuccess || cudaMalloc(&b, bytes) != cudaSuccess) {
+            cudaFree(a);
+            break;
+        }
+        cudaMemset(a, 0, bytes);
+        int pick[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int axis = 2; axis >= 0; axis--) {
+            const AxisPlan &ap = gd.ax[axis];
+            AxisTables *t = ap.n > 1 ? get_tables(P, ap.n, ap.p, ap.q, -1) : nullptr;
+            if (!t) continue;
+            for (int stage = 1; stage <= 2; stage++) {
+                const int K = stage == 1 ? ap.q : ap.p;
+                if (K > 8 || !(stage == 1 ? t->fp8_s1_l2 : t->fp8_s2_l2)) continue;
+                StageGeom g = pass_geom(gd, batch, axis);
+                float best = 1e30f;
+                for (int lpv : {4, 2}) {
+                    g.lpv = lpv;
+                    launch_stage_mode(P, *t, g, stage, a, b, 0);
+                    for (int rep = 0; rep < 2; rep++) {
+                        cudaEventRecord(ea, 0);
+                        for (int i = 0; i < 3; i++) launch_stage_mode(P, *t, g, stage, a, b, 0);
+                        cudaEventRecord(eb2, 0);
+                        cudaEventSynchronize(eb2);
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, ea, eb2);
+                        if (ms < best) {
+                            best = ms;
+                            pick[axis][stage - 1] = lpv;
+                        }
+                    }
+                }
+            }
+        }
+        for (int gi : grp)
+            for (int axis = 0; axis < 3; axis++)
+                for (int st = 0; st < 2; st++) P->grids[gi].lpv[axis][st] = pick[axis][st];
+        cudaFree(a);
+        cudaFree(b);
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb2);
+    cudaGetLastError();  // a failed candidate launch leaves no sticky error behind
+}
+
+extern "C" obfft_status obfft_plan_get_tuning(obfft_plan p, int grid, int axis, int *p_out, int *q_out,
+                                              int *lpv_stage1, int *lpv_stage2) {
+    if (!p || !p_out || !q_out || !lpv_stage1 || !lpv_stage2 || axis < 0 || axis > 2 || grid < 0 ||
+        grid >= (int)p->grids.size())
+        return set_error(OBFFT_ERR_ARG, "bad plan, grid, axis or output pointer");
+    const GridDesc &gd = p->grids[grid];
+    const AxisPlan &ap = gd.ax[axis];
+    *p_out = ap.p;
+    *q_out = ap.q;
+    *lpv_stage1 = *lpv_stage2 = 0;
+    const bool tc = p->mode == OBFFT_MODE_FP8 || p->mode == OBFFT_MODE_FP16 || p->mode == OBFFT_MODE_FP32;
+    if (!tc || ap.n == 1) return OBFFT_OK;
+    int64_t batch = p->batch;
+    if (!p->groups.empty())
+        for (const auto &grp : p->groups)
+            for (int gi : grp)
+                if (gi == grid) batch = (int64_t)grp.size();
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return set_error(OBFFT_ERR_CUDA, "device query failed");
+    const AxisTables *t = get_tables(p, ap.n, ap.p, ap.q, -1);
+    for (int stage = 1; stage <= 2; stage++) {
+        StageGeom g = pass_geom(gd, batch, axis);
+        g.lpv = gd.lpv[axis][stage - 1];
+        const bool l2 = t && (stage == 1 ? t->fp8_s1_l2 : t->fp8_s2_l2);
+        (stage == 1 ? *lpv_stage1 : *lpv_stage2) = pick_lpv(g, stage, l2, nsm);
+    }
+    return OBFFT_OK;
+}
+
 static obfft_status run_stage(obfft_plan P, const GridDesc &gd, int64_t batch, int axis, int stage,
                               const void *in, void *out, int dir, cudaStream_t s) {
-    return run_stage_geom(P, gd.ax[axis], pass_geom(gd, batch, axis), stage, in, out, dir, s);
+    StageGeom g = pass_geom(gd, batch, axis);
+    g.lpv = gd.lpv[axis][stage - 1];
+    return run_stage_geom(P, gd.ax[axis], g, stage, in, out, dir, s);
 }
 
 // The axis passes first_axis, first_axis - 1, ..., last_axis (the full

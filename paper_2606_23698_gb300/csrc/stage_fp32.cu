@@ -616,13 +616,8 @@ cudaError_t launch_stage_fp32(const AxisTables &t, const void *pab, int *status,
         Lpad = (g.L + tile - 1) / tile * tile;
         return stage == 1 ? g.L * g.p : Lpad * g.q;
     };
-    int lpv = fp8_lines_per_lane(K);
     const void *planes_l2 = stage == 1 ? t.fp8_s1_l2 : t.fp8_s2_l2;
-    if (lpv == 4 && planes_l2) {
-        int64_t lp4, lp2;
-        const int64_t b4 = (columns(4, lp4) + 511) / 512, b2 = (columns(2, lp2) + 255) / 256;
-        if ((b2 + nsm - 1) / nsm <= (b4 + nsm - 1) / nsm) lpv = 2;
-    }
+    const int lpv = pick_lpv(g, stage, planes_l2 != nullptr, nsm);
     const int tile = 128 * lpv, kslots = lpv > 1 ? 32 : K;
     ColMapT map;
     map.stage = stage;

@@ -945,6 +945,22 @@ cudaError_t fp8_upload_constants() {
     return cudaMemcpyToSymbol(c_fp8_mc, &mc, sizeof(mc));
 }
 
+int pick_lpv(const StageGeom &g, int stage, bool have_l2_planes, int nsm) {
+    const int K = stage == 1 ? g.q : g.p;
+    const int top = fp8_lines_per_lane(K);
+    if (g.lpv == top || (g.lpv == 2 && top == 4 && have_l2_planes)) return g.lpv;
+    if (top == 4 && have_l2_planes) {
+        // columns of the launch with lpv lines per lane (stage 2 pads each k2 group)
+        auto cols = [&](int lpv) {
+            const int64_t tile = 128 * lpv, Lpad = (g.L + tile - 1) / tile * tile;
+            return stage == 1 ? g.L * g.p : Lpad * g.q;
+        };
+        const int64_t b4 = (cols(4) + 511) / 512, b2 = (cols(2) + 255) / 256;
+        if ((b2 + nsm - 1) / nsm <= (b4 + nsm - 1) / nsm) return 2;
+    }
+    return top;
+}
+
 size_t fp8_smem_bytes(int Kout, int npad) {
     size_t stage_bytes = (size_t)Kout * 128 / 8 * PA_ROWB + 128;
     return ((stage_bytes + 1023) & ~(size_t)1023) + 2 * FP8_BPLANES * (size_t)npad * 32 + PA_N * 64;
@@ -988,13 +1004,8 @@ static cudaError_t launch_stage_carrier(const AxisTables &t, const void *pab, in
         Lpad = (g.L + tile - 1) / tile * tile;
         return stage == 1 ? g.L * g.p : Lpad * g.q;
     };
-    int lpv = fp8_lines_per_lane(K);
     const void *planes_l2 = stage == 1 ? t.fp8_s1_l2 : t.fp8_s2_l2;
-    if (lpv == 4 && planes_l2) {
-        int64_t lp4, lp2;
-        const int64_t b4 = (columns(4, lp4) + 511) / 512, b2 = (columns(2, lp2) + 255) / 256;
-        if ((b2 + nsm - 1) / nsm <= (b4 + nsm - 1) / nsm) lpv = 2;
-    }
+    const int lpv = pick_lpv(g, stage, planes_l2 != nullptr, nsm);
     const int tile = 128 * lpv;
     const int kslots = lpv > 1 ? 32 : K;
     ColMapT map;

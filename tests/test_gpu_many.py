@@ -24,7 +24,9 @@ def built():
 
 
 @pytest.mark.parametrize("mode", ["fp8", "int8", "fp64", "fp16"])
-def test_many_matches_single_plans_and_replays(mode):
+def test_many_matches_single_plans_and_replays(mode, monkeypatch):
+    # untuned: the single-grid plans use the default splits too
+    monkeypatch.setenv("OBFFT_AUTOTUNE", "0")
     from paper_2606_23698_gb300 import Plan, PlanMany
     xs = [S.complex_gaussian(S.SEED_UNEVEN + i, d).to("cuda") for i, d in enumerate(DIMS)]
     pm = PlanMany(DIMS, mode=mode)
@@ -74,10 +76,11 @@ print("splits", sp)
     assert "splits" in r.stdout
 
 
-def test_many_single_grid_and_all_identical_grids():
+def test_many_single_grid_and_all_identical_grids(monkeypatch):
     """Edge cases of the grouping: a plan of one grid, a plan whose grids all
     share one shape (one batched group), and exec_many on a one-grid plan made
     by obfft_plan_create."""
+    monkeypatch.setenv("OBFFT_AUTOTUNE", "0")  # compared with untuned single-grid plans
     from paper_2606_23698_gb300 import Plan, PlanMany, _lib
     d = (8, 12, 16)
     for dims in ([d], [d, d, d]):
@@ -150,3 +153,29 @@ def test_many_rejects_overlapping_ranges():
             assert "overlap" in str(ei.value)
     finally:
         _lib.obfft_destroy(pm)
+
+
+@pytest.mark.parametrize("mode", ["fp8", "fp16"])
+def test_default_tuning_reported_and_exact(mode):
+    """Multi-grid plans are tuned by default (splits and lines per TMEM lane);
+    obfft_plan_get_tuning reports valid choices and the outputs stay
+    bit-exact against the oracle with the reported splits."""
+    from paper_2606_23698_gb300 import PlanMany, _lib
+    dims = [(64, 64, 64), (16, 32, 96), (64, 64, 64), (8, 8, 8)]
+    xs = [S.complex_uniform(S.SEED_UNEVEN + 300 + i, d).to("cuda") for i, d in enumerate(dims)]
+    pm = PlanMany(dims, mode=mode)
+    outs = pm.exec(xs, dir=-1)
+    torch.cuda.synchronize()
+    for i, d in enumerate(dims):
+        sp = []
+        for a in range(3):
+            p, q, l1, l2 = _lib.obfft_plan_get_tuning(pm.handle, i, a)
+            assert p * q == d[a] and max(p, q) <= 32
+            for K, lpv in ((q, l1), (p, l2)):
+                if d[a] > 1:
+                    top = 4 if K <= 8 else (2 if K <= 16 else 1)
+                    assert lpv == top or (top == 4 and lpv == 2), (d, a, K, lpv)
+            sp.append((p, q))
+        want = oracle_full(xs[i].cpu().numpy(), tuple(sp), -1)
+        assert bits_equal(outs[i].cpu().numpy(), want), d
+    pm.close()
