@@ -220,6 +220,11 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     constexpr uint32_t PLANE_B = NPAD * NPAD * 2, BUF_PLANES = 8, SBO = 16 * NPAD;
     constexpr uint32_t ACC = 4 * NPAD;  // columns of one accumulator set (two classes, Re | Im)
     constexpr uint32_t APL = 2 * ACC;   // first A buffer, after the two accumulator sets
+    // Phase-A row blocks from column 256 on (over the A buffers, whose last
+    // MMAs have completed): they never overlap an accumulator set, which other
+    // warps may still be reading when a warp presets its first blocks
+    constexpr uint32_t PA_COL0 = 2 * ACC;
+    static_assert(PA_COL0 + 8 * PA32_N <= 512, "a Phase-A wave within the 512 TMEM columns");
     extern __shared__ __align__(1024) uint8_t smem[];
     const ModConsts32 &mc = c_fp32_mc;
     __shared__ int colpart[4][128];
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     if (ok) {
         constexpr int per_wave = 8;
         auto preset = [&](int bi) {
-            const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA32_N);
+            const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(bi * PA32_N);
             tmem_st16_const(ta, 0x4B000000u);
             tmem_st16_const(ta + 16, 0x4B000000u);
         };
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
                 for (int bi = 0; bi < nb; bi++) {
                     // a row block is 16 row groups: 16 x PA32_ROWB bytes per output slot
                     const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b0, bi) * (16 * PA32_ROWB / 16));
-                    tc_mma_f16(tmem + (uint32_t)(bi * PA32_N), ad, bdescA, idescA, 1);
+                    tc_mma_f16(tmem + PA_COL0 + (uint32_t)(bi * PA32_N), ad, bdescA, idescA, 1);
                 }
                 tc_commit(smem_u32(&mbar[6]));
                 pendA = true;
@@ -509,7 +514,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
             tc_fence_after();
             if (okA) {
                 for (int bi = qd; bi < nb; bi += 4) {
-                    const uint32_t ta = tmem + lanebase + (uint32_t)(bi * PA32_N);
+                    const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(bi * PA32_N);
                     uint32_t a8[8], a4[4], b8[8], b4[4];
                     tmem_ld8(ta, a8);
                     tmem_ld4(ta + 8, a4);

@@ -70,6 +70,12 @@ constexpr int FP8_BPLANES = 12;  // planes of one modulus' constant operand buff
 constexpr int PA_N = 48;          // Phase A output columns (Re 24 | Im 24)
 constexpr int PA_GSLOTS = 2;      // Phase-A accumulator slots per quarter-warp group (8 x 48 TMEM columns)
 constexpr int PA_SLOTS = 4 * PA_GSLOTS;
+// TMEM column of the first Phase-A slot: the slots take columns 128..511, so
+// they never overlap the FP16 carrier's accumulator set of the last modulus
+// (columns 0..127), which other warps may still be reading when a warp presets
+// its first slots
+constexpr uint32_t PA_COL0 = 128;
+static_assert(PA_COL0 + PA_SLOTS * PA_N <= 512, "Phase-A slots within the 512 TMEM columns");
 constexpr int PA_ROWB = 384;      // bytes per 8-row group of the staging (3 K-chunks)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
@@ -101,8 +107,10 @@ constexpr int FP8_WARPS = 16;
 __constant__ ModConsts c_fp8_mc;
 constexpr uint32_t APL_BASE = 320, APL_COLS = 48;  // two A buffers
 // FP16 carrier: TMEM columns of one accumulator set (two classes, Re | Im, at
-// npad = 32); the second set follows the first, below the A buffers
+// npad = 32); the second set follows the first, below the A buffers.  Modulus
+// k uses set (k ^ (NMOD - 1)) & 1, so the last modulus uses set 0.
 constexpr uint32_t F16_ACC = 128;
+__device__ __forceinline__ uint32_t f16_acc_col(int k) { return (uint32_t)((k ^ (NMOD - 1)) & 1) * F16_ACC; }
 
 template <int NPAD>
 struct Fp8Cfg {
@@ -465,12 +473,21 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     uint8_t *sIn = sStage;
     __shared__ int64_t s_e0;  // stage 1: first element of the input tile
     (void)gmc;
+    // Thread 32 issues every bulk copy into shared memory; on the failure path
+    // it waits (bounded) for the last copy into each barrier before the CTA
+    // exits.  Kept in shared memory (written and read by thread 32 only, so no
+    // registers are held through the pipeline): the last modulus whose
+    // constants went into B buffer 0 / 1, and whether the Phase-A constants
+    // were requested.
+    __shared__ int pf_last[3];
     if (w == 0) {
         tmem_alloc(smem_u32(&tmem_holder), 512);
     } else if (w == 1) {
         const InputTile itile = input_tile(map, ncols, cbase, TILE);
         if (lane == 0) {
             if (CAR) fail[0] = fail[1] = 0;
+            pf_last[0] = pf_last[1] = -1;
+            pf_last[2] = 0;
             s_e0 = itile.e0;
             for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
             for (int b = 0; b < PA_SLOTS; b++) {
@@ -485,10 +502,12 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             if (!CAR) {
                 mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
                 tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
+                pf_last[2] = 1;
             }
             const uint32_t bytes0 = CC::planes_of(0) * planeB;
             mbar_expect_tx(smem_u32(&mbar[0]), bytes0);
             tma_bulk_g2s(smem_u32(sB0), gplanes, bytes0, smem_u32(&mbar[0]));
+            pf_last[0] = 0;
         }
     } else if (w == 2) {
         // the tile about one wave of CTAs ahead, most likely next on some SM
@@ -502,7 +521,8 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
-    // classes 2..4 start at zero (issue_modulus_nm)
+    // E4M3 classes 2..4 start at zero (issue_modulus_nm)
+    if (!CAR)
 #pragma unroll
     for (int cl = 2; cl < 5; cl++)
 #pragma unroll
@@ -639,6 +659,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         mbar_expect_tx(smem_u32(&mbar[k & 1]), bytes);
         tma_bulk_g2s(smem_u32(sB0 + (k & 1) * CC::BUF_PLANES * planeB), gplanes + (size_t)CC::plane_offset(k) * planeB,
                      bytes, smem_u32(&mbar[k & 1]));
+        pf_last[k & 1] = k;
     };
     auto issue = [&](int k) -> bool {
         if (!mbar_wait(smem_u32(&mbar[k & 1]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT)) return false;
@@ -646,7 +667,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         const uint32_t apl = tmem + APL_BASE + (uint32_t)(k & 1) * CC::A_COLS;
         const int kind = fp8_kind(k);
         if constexpr (CAR)
-            issue_modulus_f16<NPAD>(tmem + (uint32_t)(k & 1) * F16_ACC, apl, bd);
+            issue_modulus_f16<NPAD>(tmem + f16_acc_col(k), apl, bd);
         else if (kind == KIND_SQ)
             issue_modulus_nm<KIND_SQ>(tmem, apl, bd, NPAD);
         else if (kind == KIND_B9)
@@ -709,9 +730,10 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 } else if (k + 2 == NSTEP) {
                     mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
                     tma_bulk_g2s(smem_u32(sPAB), pab, PA_N * 64, smem_u32(&mbar[4]));
+                    pf_last[2] = 1;
                 }
             }
-            const uint32_t tre = tmem + lanebase + (uint32_t)(k & 1) * F16_ACC + (uint32_t)(qd * OPT);
+            const uint32_t tre = tmem + lanebase + f16_acc_col(k) + (uint32_t)(qd * OPT);
             epilogue_modulus<KIND_F16, OPT>(tre, tre + NPAD, NPAD, mc, k, sStage, c, qd, Kout, dres, KS * hl, K);
         }
     } else {
@@ -770,7 +792,7 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     int pa_last = -1;                            // leader: last block whose MMAs it issued
     auto gslot = [&](int b) { return PA_GSLOTS * (b & 3) + ((b >> 2) % PA_GSLOTS); };
     auto preset = [&](int b) {
-        const uint32_t ta = tmem + lanebase + (uint32_t)(gslot(b) * PA_N);
+        const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(gslot(b) * PA_N);
         tmem_st16_const(ta, 0x4B000000u);
         tmem_st16_const(ta + 16, 0x4B000000u);
         tmem_st16_const(ta + 32, 0x4B000000u);
@@ -807,32 +829,23 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
             // a row block's descriptor lies 16 x PA_ROWB bytes (in 16-byte
             // units) per output slot past the staging start
             const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b) * (16 * PA_ROWB / 16));
-            const uint32_t d = tmem + (uint32_t)(gslot(b) * PA_N);
+            const uint32_t d = tmem + PA_COL0 + (uint32_t)(gslot(b) * PA_N);
             tc_mma_f16(d, ad, bdescA0, idescA, 1);
             tc_mma_f16(d, ad + 16, bdescA1, idescA, 1);  // + 256 bytes: K 16..31
             tc_commit(smem_u32(&pa_full[gslot(b)]));
             pa_last = b;
         };
         // the 42 used accumulator words of a row block: Re 0..20, Im 24..44
+        // (loaded straight into the word array: Re words 0..20 from columns
+        // 0..20, Im words 21..41 from columns 24..44)
         auto load_block = [&](int b, uint32_t (&wv)[42]) {
-            const uint32_t ta = tmem + lanebase + (uint32_t)(gslot(b) * PA_N);
-            uint32_t a[16], bb[4], c16[16], d[4];
-            tmem_ld16(ta, a);
-            tmem_ld4(ta + 16, bb);
+            const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(gslot(b) * PA_N);
+            tmem_ld16(ta, *reinterpret_cast<uint32_t(*)[16]>(&wv[0]));
+            tmem_ld4(ta + 16, *reinterpret_cast<uint32_t(*)[4]>(&wv[16]));
             tmem_ld1(ta + 20, wv[20]);
-            tmem_ld16(ta + 24, c16);
-            tmem_ld4(ta + 40, d);
+            tmem_ld16(ta + 24, *reinterpret_cast<uint32_t(*)[16]>(&wv[21]));
+            tmem_ld4(ta + 40, *reinterpret_cast<uint32_t(*)[4]>(&wv[37]));
             tmem_ld1(ta + 44, wv[41]);
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                wv[i] = a[i];
-                wv[21 + i] = c16[i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                wv[16 + i] = bb[i];
-                wv[37 + i] = d[i];
-            }
         };
         auto after_wait = [&](uint32_t (&wv)[42]) {
 #pragma unroll
@@ -908,8 +921,15 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 mbar_wait(smem_u32(&mbar[2 + (j & 1)]), (uint32_t)((j >> 1) & 1), WAIT_LIMIT);
         }
         if (!CAR) mbar_wait(smem_u32(&mbar[2]), mph[0], WAIT_LIMIT);
+    }
+    if (!ok && tid == 32) {
+        // copies into shared memory: the input tile, the Phase-A constants and
+        // the last constant planes of each B buffer (an earlier copy into the
+        // same buffer completed before the MMAs that preceded the later copy)
         mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT);
-        mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT);
+        if (pf_last[2]) mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT);
+        for (int b = 0; b < 2; b++)
+            if (pf_last[b] >= 0) mbar_wait(smem_u32(&mbar[b]), (uint32_t)((pf_last[b] >> 1) & 1), WAIT_LIMIT);
     }
     // Phase A on the failure path: each leader's last commit completes once
     // every MMA it issued has (the waits are bounded)

@@ -234,7 +234,8 @@ def test_fp32_exec_host_matches_device_exec(mode):
     assert torch.equal(yh.view(torch.float32), yd.view(torch.float32))
 
 
-def test_fp32_many_matches_single_plans():
+def test_fp32_many_matches_single_plans(monkeypatch):
+    monkeypatch.setenv("OBFFT_AUTOTUNE", "0")  # compared with untuned single-grid plans
     from paper_2606_23698_gb300 import PlanMany
     dims = [(16, 16, 16), (8, 24, 12), (32, 32, 32), (4, 4, 64)]
     xs = [S.complex_gaussian(20 + i, d, device="cuda").to(torch.complex64) for i, d in enumerate(dims)]
