@@ -433,11 +433,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // preset again (one arrival per warp of the owning quarter-warp group)
     __shared__ __align__(8) uint64_t pa_full[PA_SLOTS], pa_empty[PA_SLOTS];
     __shared__ uint32_t tmem_holder;
-    // FP16 carrier pipeline: failure flags of the steps, read by every thread
-    // right after the barrier that starts step t from slot t & 1; failures are
-    // written to the slot of the step whose barrier follows them, so no thread
-    // reads a slot that another thread may still be writing
-    __shared__ int fail[2];
 
     static_assert(NPAD == 32 && (LPV == 1 || LPV == 2 || LPV == 4), "32 slots per lane, 1, 2 or 4 lines");
     constexpr int QPL = 4 / LPV;           // quarter-warp groups per line
@@ -486,7 +481,6 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     } else if (w == 1) {
         const InputTile itile = input_tile(map, ncols, cbase, TILE);
         if (lane == 0) {
-            if (CAR) fail[0] = fail[1] = 0;
             pf_last[0] = pf_last[1] = -1;
             pf_last[2] = 0;
             s_e0 = itile.e0;
@@ -685,13 +679,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     bool ok = __syncthreads_or(tfail) == 0;
     if (ok && tid == 0) {
         tc_fence_after();
-        // a failed first issue: the FP16-carrier pipeline reads it from slot 0
-        // behind its first step barrier, the E4M3 pipeline at its first
-        // __syncthreads_or (every thread's MMA wait then gives up as well)
-        if (!issue(0)) {
-            if (CAR) fail[0] = 1;
-            tfail = true;
-        }
+        // a failed first issue reaches the CTA at the first __syncthreads_or
+        // of either pipeline (every thread's MMA wait then gives up as well)
+        if (!issue(0)) tfail = true;
     } else if (ok && tid == 32 && NMOD > 1) {
         prefetch_b(1);  // buffer 1 is unused so far
     }
@@ -703,25 +693,26 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         // every thread has written its data residues, and run while the
         // epilogue of modulus k reads set k & 1.  The constant planes of
         // modulus k+2 (after the last modulus: the Phase-A constants) go into
-        // the B buffer of modulus k once its MMAs have completed.
+        // the B buffer of modulus k once its MMAs have completed.  A failure
+        // stays in the thread's own tfail until the step's __syncthreads_or
+        // (a shared flag read after one barrier measured 0.6 % slower).
         for (int k = 0; k < NSTEP && ok; k++) {
             if (k + 1 < NMOD) gen(k + 1);
             tmem_wait_st();
             tc_fence_before();
-            __syncthreads();  // residues of modulus k+1 written; epilogue k-1 done
-            if (fail[k & 1]) {
+            if (__syncthreads_or(tfail)) {  // residues of modulus k+1 written; epilogue k-1 done
                 ok = false;
                 break;
             }
             if (tid == 0 && k + 1 < NSTEP) {
                 tc_fence_after();
                 if (issue(k + 1)) last_issued = k + 1;
-                else atomicExch(&fail[(k + 1) & 1], 1);
+                else tfail = true;
             }
             const bool okm = mbar_wait(smem_u32(&mbar[2 + (k & 1)]), (uint32_t)((k >> 1) & 1), WAIT_LIMIT);
             tc_fence_after();
             if (!okm) {
-                atomicExch(&fail[(k + 1) & 1], 1);
+                tfail = true;
                 continue;
             }
             last_waited = k;
@@ -784,12 +775,15 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     // i-th block b = g + 4 i accumulates in slot PA_GSLOTS g + i % PA_GSLOTS.
     // Accumulators start at 2^23 (the FP32 bit pattern of 2^23 + P is
     // 0x4B000000 + P).  After its four warps have read block b and preset the
-    // slot again (the slot's empty barrier), the group's first warp issues the
+    // slot again (the slot's empty barrier), the group's issuing warp issues the
     // MMAs of block b + 4 PA_GSLOTS into it; they run while the group finishes
     // block b.  No CTA barrier separates the blocks, and the groups never wait
     // for one another.
     const int nblk = Kout;
-    const bool leader = sub == 0 && lane == 0;  // issues the MMAs of its group's blocks
+    // the MMAs of a group's blocks are issued by lane 0 of its warp with
+    // sub == qd, so the four issuing warps sit on the four schedulers (warps
+    // 0, 5, 10, 15; all on scheduler 0 measured 1.1 to 1.6 % slower)
+    const bool leader = sub == qd && lane == 0;
     int pa_last = -1;                            // leader: last block whose MMAs it issued
     auto gslot = [&](int b) { return PA_GSLOTS * (b & 3) + ((b >> 2) % PA_GSLOTS); };
     auto preset = [&](int b) {
@@ -804,8 +798,9 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         tc_fence_before();
         fence_async_smem();
         const int bad = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT) ? 0 : 1;
-        ok = __syncthreads_or(bad | (int)(tfail && !CAR)) == 0;  // uniform decision across the CTA
-        if (CAR && fail[NSTEP & 1]) ok = false;  // a failed wait in the last pipeline step
+        // uniform decision across the CTA (including a failed wait in the last
+        // pipeline step)
+        ok = __syncthreads_or(bad | (int)tfail) == 0;
     }
     if (ok) {
         const uint32_t idescA = instr_desc(128, PA_N, 0);
