@@ -33,6 +33,7 @@ namespace obfft {
 constexpr int F32_WARPS = 16;
 constexpr int PA32_N = 32;       // Phase A accumulator columns per row block (Re 16 | Im 16)
 constexpr int PA32_ROWB = 256;   // bytes per 8-row group of the staging (2 K-chunks of 8 FP16)
+constexpr int PA32_GSLOTS = 2;   // Phase-A accumulator slots per quarter-warp group (8 x 32 TMEM columns)
 constexpr uint32_t WAIT_LIMIT32 = 1u << 22;
 
 struct ModConsts32 {
@@ -204,7 +205,7 @@ __device__ __forceinline__ void prefetch_input_tile32(const ColMapT &map, const 
 // 4 (b + 1) npad) (class cl, Re at 2 cl npad, Im npad later), so that the MMAs
 // of modulus k+1 run while the epilogue of modulus k reads its set; FP16 A
 // buffers of the data residues at 8 npad + b npad (x_R in the first npad / 2
-// columns, x_I in the next); Phase A reuses [0, 8 x 32).
+// columns, x_I in the next); the eight Phase-A slots take [256, 512).
 // LPV = 2 or 4 (K <= 16 or K <= 8, NPAD = 32): LPV lines per TMEM lane, as
 // in the FP8 / FP16-carrier stage kernel: line h in slots [KS h, KS h + KS)
 // with block-diagonal constants; quarter-warp group qd works on line
@@ -220,17 +221,20 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     constexpr uint32_t PLANE_B = NPAD * NPAD * 2, BUF_PLANES = 8, SBO = 16 * NPAD;
     constexpr uint32_t ACC = 4 * NPAD;  // columns of one accumulator set (two classes, Re | Im)
     constexpr uint32_t APL = 2 * ACC;   // first A buffer, after the two accumulator sets
-    // Phase-A row blocks from column 256 on (over the A buffers, whose last
-    // MMAs have completed): they never overlap an accumulator set, which other
-    // warps may still be reading when a warp presets its first blocks
+    // Phase-A slots from column 256 on (over the A buffers, whose last MMAs
+    // have completed): they never overlap an accumulator set, which other
+    // warps may still be reading when a warp presets its first slots
     constexpr uint32_t PA_COL0 = 2 * ACC;
-    static_assert(PA_COL0 + 8 * PA32_N <= 512, "a Phase-A wave within the 512 TMEM columns");
+    static_assert(PA_COL0 + 4 * PA32_GSLOTS * PA32_N <= 512, "the Phase-A slots within the 512 TMEM columns");
     extern __shared__ __align__(1024) uint8_t smem[];
     const ModConsts32 &mc = c_fp32_mc;
     __shared__ int colpart[4][128];
     // 0,1: B planes (TMA, per buffer), 2,3: MMAs of modulus k (per accumulator
-    // set k & 1), 4: Phase-A B, 5: input tile, 6: Phase-A MMAs
-    __shared__ __align__(8) uint64_t mbar[7];
+    // set k & 1), 4: Phase-A B, 5: input tile
+    __shared__ __align__(8) uint64_t mbar[6];
+    // Phase-A slots: MMAs complete (one commit) / slot read and preset again
+    // (one arrival per warp of the owning quarter-warp group)
+    __shared__ __align__(8) uint64_t pa_full[4 * PA32_GSLOTS], pa_empty[4 * PA32_GSLOTS];
     __shared__ uint32_t tmem_holder;
 
     static_assert(LPV == 1 || (NPAD == 32 && (LPV == 2 || LPV == 4)), "1, 2 or 4 lines per lane");
@@ -261,7 +265,11 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         const InputTile32 itile = input_tile32(map, ncols, cbase, TILE);
         if (lane == 0) {
             s_e0 = itile.e0;
-            for (int b = 0; b < 7; b++) mbar_init(smem_u32(&mbar[b]), 1);
+            for (int b = 0; b < 6; b++) mbar_init(smem_u32(&mbar[b]), 1);
+            for (int b = 0; b < 4 * PA32_GSLOTS; b++) {
+                mbar_init(smem_u32(&pa_full[b]), 1);
+                mbar_init(smem_u32(&pa_empty[b]), 4);
+            }
             mbar_fence_init();
         }
         __syncwarp();
@@ -463,102 +471,115 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         if (tid == 32 && k + 2 < NMOD32) prefetch_b(k + 2);  // B buffer k & 1 is free again
         epilogue(k);
     }
-    uint32_t mph = 0u;     // next phase parity of the Phase-A MMA barrier mbar[6]
-    bool pendA = false;    // thread 0: a Phase-A commit is outstanding
-
     // ---------------- CRT Phase A (FP16 tensor cores), then Phase B + pack ----------------
+    // As in the FP8 / FP16-carrier stage kernel: row block b (one output slot,
+    // N = 32 accumulators) belongs to quarter-warp group g = b & 3, which owns
+    // PA32_GSLOTS slots of 32 columns; its issuing warp (sub == qd, one per
+    // scheduler) issues the MMA of block b + 4 PA32_GSLOTS into the slot of
+    // block b once the group's four warps have read and preset it.
+    const int nblk = Kout;
+    const bool leader = sub == qd && lane == 0;
+    int pa_last = -1;  // leader: last block whose MMA it issued
+    auto gslot = [&](int b) { return PA32_GSLOTS * (b & 3) + ((b >> 2) % PA32_GSLOTS); };
+    auto preset = [&](int b) {
+        const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(gslot(b) * PA32_N);
+        tmem_st16_const(ta, 0x4B000000u);
+        tmem_st16_const(ta + 16, 0x4B000000u);
+    };
     if (ok) {
-        constexpr int per_wave = 8;
-        auto preset = [&](int bi) {
-            const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(bi * PA32_N);
-            tmem_st16_const(ta, 0x4B000000u);
-            tmem_st16_const(ta + 16, 0x4B000000u);
-        };
-        for (int bi = qd; bi < min(per_wave, Kout); bi += 4) preset(bi);
+        for (int i = 0; i < PA32_GSLOTS && qd + 4 * i < nblk; i++) preset(qd + 4 * i);
         tmem_wait_st();
         tc_fence_before();
         fence_async_smem();
         const bool okp = mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT32);
         ok = __syncthreads_or(bad || !okp) == 0;
+    }
+    if (ok) {
         const uint32_t idescA = instr_desc(128, PA32_N, 0);
         const uint64_t adescA = smem_desc(smem_u32(sStage), 128, PA32_ROWB);
         const uint64_t bdescA = smem_desc(smem_u32(sPAB), 128, 256);
         const uint64_t M = mc.M;
         const int64_t halfM = mc.halfM;
-        // output slot of row block bi of the wave starting at b0 (with LPV
-        // lines per lane, the thread finishing blocks qd and qd + 4 stays on
-        // its own line; see the FP8 stage kernel)
-        auto kout_of = [&](int b0, int bi) -> int {
-            if constexpr (LPV == 1) return b0 + bi;
+        // output slot of row block b (with LPV lines per lane, the thread
+        // finishing the blocks b = qd (mod 4) stays on its own line; see the
+        // FP8 stage kernel)
+        auto kout_of = [&](int b) -> int {
+            const int b0 = b & ~7, bi = b & 7;
+            if constexpr (LPV == 1) return b;
             else if constexpr (LPV == 2) return KS * ((bi & 3) >> 1) + (b0 >> 1) + 2 * (bi >> 2) + (bi & 1);
             else return KS * (bi & 3) + (b0 >> 2) + (bi >> 2);
         };
-        for (int b0 = 0; b0 < Kout && ok; b0 += per_wave) {
-            const int nb = min(per_wave, Kout - b0);
-            const int nb_next = min(per_wave, Kout - b0 - per_wave);
-            if (tid == 0) {
-                tc_fence_after();
-                for (int bi = 0; bi < nb; bi++) {
-                    // a row block is 16 row groups: 16 x PA32_ROWB bytes per output slot
-                    const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b0, bi) * (16 * PA32_ROWB / 16));
-                    tc_mma_f16(tmem + PA_COL0 + (uint32_t)(bi * PA32_N), ad, bdescA, idescA, 1);
-                }
-                tc_commit(smem_u32(&mbar[6]));
-                pendA = true;
-            }
-            const bool okA = mbar_wait(smem_u32(&mbar[6]), mph, WAIT_LIMIT32);
-            if (okA) {
-                mph ^= 1u;
-                pendA = false;
-            }
+        auto issue_block = [&](int b) {
             tc_fence_after();
-            if (okA) {
-                for (int bi = qd; bi < nb; bi += 4) {
-                    const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(bi * PA32_N);
-                    uint32_t a8[8], a4[4], b8[8], b4[4];
-                    tmem_ld8(ta, a8);
-                    tmem_ld4(ta + 8, a4);
-                    tmem_ld8(ta + 16, b8);
-                    tmem_ld4(ta + 24, b4);
-                    tmem_wait_ld();
-                    uint32_t wr[11], wi[11];
+            // a row block is 16 row groups: 16 x PA32_ROWB bytes per output slot
+            const uint64_t ad = adescA + (uint64_t)((uint32_t)kout_of(b) * (16 * PA32_ROWB / 16));
+            tc_mma_f16(tmem + PA_COL0 + (uint32_t)(gslot(b) * PA32_N), ad, bdescA, idescA, 1);
+            tc_commit(smem_u32(&pa_full[gslot(b)]));
+            pa_last = b;
+        };
+        if (leader)
+            for (int i = 0; i < PA32_GSLOTS && qd + 4 * i < nblk; i++) issue_block(qd + 4 * i);
+        for (int i = 0, b = qd; b < nblk; i++, b += 4) {
+            const int sl = gslot(b);
+            const uint32_t use = (uint32_t)((i / PA32_GSLOTS) & 1);  // phase parity of this use of the slot
+            const bool okb = mbar_wait(smem_u32(&pa_full[sl]), use, WAIT_LIMIT32);
+            tc_fence_after();
+            const uint32_t ta = tmem + lanebase + PA_COL0 + (uint32_t)(sl * PA32_N);
+            uint32_t a8[8], a4[4], b8[8], b4[4];
+            tmem_ld8(ta, a8);
+            tmem_ld4(ta + 8, a4);
+            tmem_ld8(ta + 16, b8);
+            tmem_ld4(ta + 24, b4);
+            tmem_wait_ld();
+            uint32_t wr[11], wi[11];
 #pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        wr[i] = a8[i];
-                        wi[i] = b8[i];
-                    }
+            for (int j = 0; j < 8; j++) {
+                wr[j] = a8[j];
+                wi[j] = b8[j];
+            }
 #pragma unroll
-                    for (int i = 0; i < 3; i++) {
-                        wr[8 + i] = a4[i];
-                        wi[8 + i] = b4[i];
-                    }
+            for (int j = 0; j < 3; j++) {
+                wr[8 + j] = a4[j];
+                wi[8 + j] = b4[j];
+            }
 #pragma unroll
-                    for (int i = 0; i < 11; i++) asm volatile("" : "+r"(wr[i]), "+r"(wi[i]));
-                    if (bi < nb_next) preset(bi);
-                    int64_t zr = 0, zi = 0, Rr = 0, Ri = 0;
-                    const float re = crt_pack32(wr, e - 46, M, halfM, DBG ? &zr : nullptr, DBG ? &Rr : nullptr);
-                    const float im = crt_pack32(wi, e - 46, M, halfM, DBG ? &zi : nullptr, DBG ? &Ri : nullptr);
-                    const int kl = kout_of(b0, bi) - KS * hl;  // output index within this thread's line
-                    if (cvalid && kl < K) out[obase + (int64_t)kl * ostride] = make_float2(re, im);
-                    if (DBG && drow >= 0 && kl < K) {
-                        const int64_t o = drow * K + kl;
-#pragma unroll
-                        for (int i = 0; i < 11; i++) {
-                            dbg.acc[(o * 2 + 0) * 11 + i] = wr[i];
-                            dbg.acc[(o * 2 + 1) * 11 + i] = wi[i];
-                        }
-                        dbg.zhat[o * 2] = zr;
-                        dbg.zhat[o * 2 + 1] = zi;
-                        const uint32_t sr = (uint32_t)(Rr >> 63), si = (uint32_t)(Ri >> 63);
-                        dbg.put_R128(drow, kl, 0, (uint32_t)Rr, (uint32_t)((uint64_t)Rr >> 32), sr, sr);
-                        dbg.put_R128(drow, kl, 1, (uint32_t)Ri, (uint32_t)((uint64_t)Ri >> 32), si, si);
-                    }
+            for (int j = 0; j < 11; j++) asm volatile("" : "+r"(wr[j]), "+r"(wi[j]));
+            const int bn = b + 4 * PA32_GSLOTS;  // the group's next block in this slot
+            if (bn < nblk) {
+                preset(bn);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&pa_empty[sl]));
+                if (leader) {
+                    if (mbar_wait(smem_u32(&pa_empty[sl]), use, WAIT_LIMIT32)) issue_block(bn);
+                    else bad = true;
                 }
             }
-            tmem_wait_st();
-            tc_fence_before();
-            if (__syncthreads_or(!okA)) ok = false;
+            if (!okb) {
+                bad = true;
+                continue;
+            }
+            int64_t zr = 0, zi = 0, Rr = 0, Ri = 0;
+            const float re = crt_pack32(wr, e - 46, M, halfM, DBG ? &zr : nullptr, DBG ? &Rr : nullptr);
+            const float im = crt_pack32(wi, e - 46, M, halfM, DBG ? &zi : nullptr, DBG ? &Ri : nullptr);
+            const int kl = kout_of(b) - KS * hl;  // output index within this thread's line
+            if (cvalid && kl < K) out[obase + (int64_t)kl * ostride] = make_float2(re, im);
+            if (DBG && drow >= 0 && kl < K) {
+                const int64_t o = drow * K + kl;
+#pragma unroll
+                for (int j = 0; j < 11; j++) {
+                    dbg.acc[(o * 2 + 0) * 11 + j] = wr[j];
+                    dbg.acc[(o * 2 + 1) * 11 + j] = wi[j];
+                }
+                dbg.zhat[o * 2] = zr;
+                dbg.zhat[o * 2 + 1] = zi;
+                const uint32_t sr = (uint32_t)(Rr >> 63), si = (uint32_t)(Ri >> 63);
+                dbg.put_R128(drow, kl, 0, (uint32_t)Rr, (uint32_t)((uint64_t)Rr >> 32), sr, sr);
+                dbg.put_R128(drow, kl, 1, (uint32_t)Ri, (uint32_t)((uint64_t)Ri >> 32), si, si);
+            }
         }
+        ok = __syncthreads_or(bad) == 0;
     }
     if (!ok && tid == 0) {
         atomicExch(status, (int)OBFFT_ERR_TIMEOUT);
@@ -566,10 +587,13 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         // TMEM is freed and the CTA exits
         for (int j = last_waited + 1; j <= last_issued; j++)
             mbar_wait(smem_u32(&mbar[2 + (j & 1)]), (uint32_t)((j >> 1) & 1), WAIT_LIMIT32);
-        if (pendA) mbar_wait(smem_u32(&mbar[6]), mph, WAIT_LIMIT32);
         if (tma_in) mbar_wait(smem_u32(&mbar[5]), 0, WAIT_LIMIT32);
         mbar_wait(smem_u32(&mbar[4]), 0, WAIT_LIMIT32);
     }
+    // Phase A on the failure path: each leader's last commit completes once
+    // every MMA it issued has (the waits are bounded)
+    if (!ok && leader && pa_last >= 0)
+        mbar_wait(smem_u32(&pa_full[gslot(pa_last)]), (uint32_t)(((pa_last >> 2) / PA32_GSLOTS) & 1), WAIT_LIMIT32);
     tc_fence_before();
     __syncthreads();
     if (w == 0) tmem_dealloc(tmem, 512);
