@@ -150,23 +150,16 @@ __device__ __forceinline__ InputTile32 input_tile32(const ColMapT &map, int64_t 
     }
     return t;
 }
-// TMA bulk copies of the tile (warp-wide call).  Only used when every copy
-// starts and ends on a 16-byte boundary (even n and K, 16-byte aligned input).
-__device__ __forceinline__ void copy_input_tile32(const ColMapT &map, const InputTile32 &t, int K, const float2 *in,
-                                                  uint8_t *sIn, uint32_t mbar, int lane) {
-    if (map.stage == 1) {
-        if (lane == 0) mbar_expect_tx(mbar, (uint32_t)((t.e1 - t.e0) * 8));
-        __syncwarp();
-        const int64_t chunk = 512;  // elements (4 KB) per copy
-        for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
-            tma_bulk_g2s(smem_u32(sIn + (e - t.e0) * 8), in + e, (uint32_t)(min(chunk, t.e1 - e) * 8), mbar);
-    } else {
-        if (lane == 0) mbar_expect_tx(mbar, (uint32_t)(t.nvalid * K * 8));
-        __syncwarp();
-        for (int i = lane; i < t.nvalid; i += 32)
-            tma_bulk_g2s(smem_u32(sIn + (int64_t)i * (K + 2) * 8), in + t.src0 + (int64_t)i * t.n, (uint32_t)(K * 8),
-                         mbar);
-    }
+// Stage 1: TMA bulk copies of the tile (warp-wide call).  Only used when
+// every copy starts and ends on a 16-byte boundary (even n and K, 16-byte
+// aligned input).
+__device__ __forceinline__ void copy_input_tile32(const InputTile32 &t, const float2 *in, uint8_t *sIn, uint32_t mbar,
+                                                  int lane) {
+    if (lane == 0) mbar_expect_tx(mbar, (uint32_t)((t.e1 - t.e0) * 8));
+    __syncwarp();
+    const int64_t chunk = 512;  // elements (4 KB) per copy
+    for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
+        tma_bulk_g2s(smem_u32(sIn + (e - t.e0) * 8), in + e, (uint32_t)(min(chunk, t.e1 - e) * 8), mbar);
 }
 // The same tile with plain 8-byte loads by all threads of the CTA.
 __device__ __forceinline__ void load_input_tile32(const ColMapT &map, const InputTile32 &t, int K, const float2 *in,
@@ -181,20 +174,12 @@ __device__ __forceinline__ void load_input_tile32(const ColMapT &map, const Inpu
         }
     }
 }
-__device__ __forceinline__ void prefetch_input_tile32(const ColMapT &map, const InputTile32 &t, int K,
-                                                      const float2 *in, int lane) {
-    if (map.stage == 1) {
-        const int64_t chunk = 512;
-        for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + e),
-                         "r"((uint32_t)(min(chunk, t.e1 - e) * 8))
-                         : "memory");
-    } else {
-        for (int i = lane; i < t.nvalid; i += 32)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + t.src0 + (int64_t)i * t.n),
-                         "r"((uint32_t)(K * 8))
-                         : "memory");
-    }
+// Stage 1: L2 prefetch of an input tile (warp-wide call)
+__device__ __forceinline__ void prefetch_input_tile32(const InputTile32 &t, const float2 *in, int lane) {
+    const int64_t chunk = 512;
+    for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + e), "r"((uint32_t)(min(chunk, t.e1 - e) * 8))
+                     : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -270,10 +255,12 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
                 mbar_init(smem_u32(&pa_full[b]), 1);
                 mbar_init(smem_u32(&pa_empty[b]), 4);
             }
+            if (tma_in && map.stage == 2) mbar_expect_tx(smem_u32(&mbar[5]), (uint32_t)(itile.nvalid * K * 8));
             mbar_fence_init();
         }
         __syncwarp();
-        if (tma_in) copy_input_tile32(map, itile, K, in, sIn, smem_u32(&mbar[5]), lane);
+        if (tma_in && map.stage == 1) copy_input_tile32(itile, in, sIn, smem_u32(&mbar[5]), lane);
+        if (tma_in && map.stage == 2) asm volatile("bar.arrive 1, 160;" ::: "memory");  // barriers ready for warps 4..7
         if (lane == 0) {
             mbar_expect_tx(smem_u32(&mbar[4]), PA32_N * 32);
             tma_bulk_g2s(smem_u32(sPAB), pab, PA32_N * 32, smem_u32(&mbar[4]));
@@ -282,8 +269,17 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         }
     } else if (w == 2) {
         const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
-        if (tma_in && pf_ahead > 0 && nb < (int64_t)gridDim.x)
-            prefetch_input_tile32(map, input_tile32(map, ncols, nb * TILE, TILE), K, in, lane);
+        if (tma_in && map.stage == 1 && pf_ahead > 0 && nb < (int64_t)gridDim.x)
+            prefetch_input_tile32(input_tile32(map, ncols, nb * TILE, TILE), in, lane);
+    } else if (w >= 4 && w < 8 && tma_in && map.stage == 2) {
+        // stage 2: one bulk copy per column (K elements of one line), issued
+        // by four warps once warp 1 has set up the barrier (as in the FP8
+        // stage kernel)
+        const InputTile32 itile = input_tile32(map, ncols, cbase, TILE);
+        asm volatile("bar.sync 1, 160;" ::: "memory");
+        for (int i = 32 * (w - 4) + lane; i < itile.nvalid; i += 128)
+            tma_bulk_g2s(smem_u32(sIn + (int64_t)i * (K + 2) * 8), in + itile.src0 + (int64_t)i * itile.n,
+                         (uint32_t)(K * 8), smem_u32(&mbar[5]));
     }
     tc_fence_before();
     __syncthreads();
@@ -436,6 +432,20 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     // (__syncthreads_or), so every thread leaves the loop at the same step.
     int last_issued = -1;    // thread 0: the last modulus whose MMAs it issued
     int last_waited = -1;    // the last modulus whose MMAs this thread waited for
+    if (map.stage == 2) {
+        // stage 2: the tile one wave of CTAs ahead into L2 by plain prefetches
+        // after the deconstruction, one 128-byte line per thread (as in the
+        // FP8 stage kernel)
+        const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
+        if (pf_ahead > 0 && nb < (int64_t)gridDim.x) {
+            const InputTile32 pt = input_tile32(map, ncols, nb * TILE, TILE);
+            const int lpr = (K * 8 + 127) / 128;
+            for (int r = tid; r < pt.nvalid * lpr; r += F32_WARPS * 32) {
+                const int i = r / lpr, q = r - i * lpr;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(in + pt.src0 + (int64_t)i * pt.n) + q * 128));
+            }
+        }
+    }
     gen(0);
     tmem_wait_st();
     tc_fence_before();

@@ -345,40 +345,22 @@ __device__ __forceinline__ InputTile input_tile(const ColMapT &map, int64_t ncol
     }
     return t;
 }
-// Bulk copies of the input tile into shared memory (warp-wide call), completing
-// on mbar.  Stage 2: column i goes to row i of stride (K + 1) x 16 bytes, the
-// padding keeping the 16-byte reads of a warp free of bank conflicts.
-__device__ __forceinline__ void copy_input_tile(const ColMapT &map, const InputTile &t, int K, const double2 *in,
-                                                uint8_t *sIn, uint32_t mbar, int lane) {
-    if (map.stage == 1) {
-        if (lane == 0) mbar_expect_tx(mbar, (uint32_t)((t.e1 - t.e0) * 16));
-        __syncwarp();
-        const int64_t chunk = 256;  // elements (4 KB) per copy
-        for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
-            tma_bulk_g2s(smem_u32(sIn + (e - t.e0) * 16), in + e, (uint32_t)(min(chunk, t.e1 - e) * 16), mbar);
-    } else {
-        if (lane == 0) mbar_expect_tx(mbar, (uint32_t)(t.nvalid * K * 16));
-        __syncwarp();
-        for (int i = lane; i < t.nvalid; i += 32)
-            tma_bulk_g2s(smem_u32(sIn + (int64_t)i * (K + 1) * 16), in + t.src0 + (int64_t)i * t.n,
-                         (uint32_t)(K * 16), mbar);
-    }
+// Stage 1: bulk copies of the input tile (one contiguous element range) into
+// shared memory (warp-wide call), completing on mbar.
+__device__ __forceinline__ void copy_input_tile(const InputTile &t, const double2 *in, uint8_t *sIn, uint32_t mbar,
+                                                int lane) {
+    if (lane == 0) mbar_expect_tx(mbar, (uint32_t)((t.e1 - t.e0) * 16));
+    __syncwarp();
+    const int64_t chunk = 256;  // elements (4 KB) per copy
+    for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
+        tma_bulk_g2s(smem_u32(sIn + (e - t.e0) * 16), in + e, (uint32_t)(min(chunk, t.e1 - e) * 16), mbar);
 }
-// L2 prefetch of an input tile (warp-wide call)
-__device__ __forceinline__ void prefetch_input_tile(const ColMapT &map, const InputTile &t, int K, const double2 *in,
-                                                    int lane) {
-    if (map.stage == 1) {
-        const int64_t chunk = 256;
-        for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + e),
-                         "r"((uint32_t)(min(chunk, t.e1 - e) * 16))
-                         : "memory");
-    } else {
-        for (int i = lane; i < t.nvalid; i += 32)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + t.src0 + (int64_t)i * t.n),
-                         "r"((uint32_t)(K * 16))
-                         : "memory");
-    }
+// Stage 1: L2 prefetch of an input tile (warp-wide call)
+__device__ __forceinline__ void prefetch_input_tile(const InputTile &t, const double2 *in, int lane) {
+    const int64_t chunk = 256;
+    for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + e), "r"((uint32_t)(min(chunk, t.e1 - e) * 16))
+                     : "memory");
 }
 
 // The general Kulisch finish, out of line: it runs only for the rare outputs the
@@ -462,10 +444,14 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
 
     // The input tile is copied into the front of the Phase-A staging, which the
     // epilogues overwrite only after every thread has read its elements.
-    // Set-up runs on three warps at once: warp 0 allocates tensor memory (the
-    // slowest step), warp 1 initialises the barriers and issues the copies of
-    // the input tile and the first constants, warp 2 prefetches the input of
-    // the CTA one wave ahead into L2.
+    // Set-up runs on several warps at once: warp 0 allocates tensor memory,
+    // warp 1 initialises the barriers and issues the copies of the first
+    // constants and (stage 1) of the input tile, warps 4..7 (stage 2) copy the
+    // input tile's columns, and warp 2 (stage 1) prefetches the input of the
+    // CTA one wave ahead into L2.  Stage 2 prefetches that tile later, by
+    // plain per-thread prefetches after the deconstruction: its 128 columns
+    // would take one bulk prefetch each, and those held the set-up for about
+    // 5,000 cycles (the whole change: 4 % per stage pair).
     uint8_t *sIn = sStage;
     __shared__ int64_t s_e0;  // stage 1: first element of the input tile
     (void)gmc;
@@ -489,10 +475,12 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
                 mbar_init(smem_u32(&pa_full[b]), 1);
                 mbar_init(smem_u32(&pa_empty[b]), 4);
             }
+            if (map.stage == 2) mbar_expect_tx(smem_u32(&mbar[5]), (uint32_t)(itile.nvalid * K * 16));
             mbar_fence_init();
         }
         __syncwarp();
-        copy_input_tile(map, itile, K, in, sIn, smem_u32(&mbar[5]), lane);
+        if (map.stage == 1) copy_input_tile(itile, in, sIn, smem_u32(&mbar[5]), lane);
+        else asm volatile("bar.arrive 1, 160;" ::: "memory");  // barriers ready for warps 4..7
         if (lane == 0) {
             if (!CAR) {
                 mbar_expect_tx(smem_u32(&mbar[4]), PA_N * 64);
@@ -507,10 +495,20 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     } else if (w == 2) {
         // the tile about one wave of CTAs ahead, most likely next on some SM
         const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
-        if (pf_ahead > 0 && nb < (int64_t)gridDim.x)
-            prefetch_input_tile(map, input_tile(map, ncols, nb * TILE, TILE), K, in, lane);
+        if (map.stage == 1 && pf_ahead > 0 && nb < (int64_t)gridDim.x)
+            prefetch_input_tile(input_tile(map, ncols, nb * TILE, TILE), in, lane);
     } else if (w == 3 && !CAR) {
         reinterpret_cast<uint32_t *>(sStage + stage_bytes - 128)[lane] = 0u;
+    } else if (w >= 4 && w < 8 && map.stage == 2) {
+        // stage 2: one bulk copy per column (K elements of one line, to row i
+        // of stride (K + 1) x 16 bytes: the padding keeps the 16-byte reads of
+        // a warp free of bank conflicts), issued by four warps once warp 1 has
+        // set up the barrier (one warp alone took 1 % longer per stage)
+        const InputTile itile = input_tile(map, ncols, cbase, TILE);
+        asm volatile("bar.sync 1, 160;" ::: "memory");
+        for (int i = 32 * (w - 4) + lane; i < itile.nvalid; i += 128)
+            tma_bulk_g2s(smem_u32(sIn + (int64_t)i * (K + 1) * 16), in + itile.src0 + (int64_t)i * itile.n,
+                         (uint32_t)(K * 16), smem_u32(&mbar[5]));
     }
     tc_fence_before();
     __syncthreads();
@@ -673,6 +671,20 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
         return true;
     };
 
+    if (map.stage == 2) {
+        // stage 2: the tile one wave of CTAs ahead into L2 by plain prefetches,
+        // one 128-byte line per thread (one bulk prefetch per column would hold
+        // the copy engine, and the set-up with it, for microseconds)
+        const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
+        if (pf_ahead > 0 && nb < (int64_t)gridDim.x) {
+            const InputTile pt = input_tile(map, ncols, nb * TILE, TILE);
+            const int lpr = (K * 16 + 127) / 128;
+            for (int r = tid; r < pt.nvalid * lpr; r += FP8_WARPS * 32) {
+                const int i = r / lpr, q = r - i * lpr;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(in + pt.src0 + (int64_t)i * pt.n) + q * 128));
+            }
+        }
+    }
     gen(0);
     tmem_wait_st();
     tc_fence_before();
