@@ -95,10 +95,12 @@ __device__ __forceinline__ uint32_t stage_off(uint32_t row, uint32_t k) {
 // pipelined: the digits of modulus k+1 are generated (into the other TMEM
 // A-buffer) while the MMAs of modulus k run; the TMA-loaded constant planes
 // are double buffered.
-// TMEM columns: class accumulators [0,320) (class cl: Re at cl 2 npad, Im at
-// cl 2 npad + npad); A digit planes of x_R (planes 0..2) and x_I (planes 3..5)
-// of one modulus in two buffers [320,368) and [368,416); Phase A reuses
-// [0,480).  One pipeline step per modulus: its MMAs run while the next
+// TMEM columns (E4M3 digits): class accumulators [0,320) (class cl: Re at
+// cl 2 npad, Im at cl 2 npad + npad); A digit planes of x_R (planes 0..2) and
+// x_I (planes 3..5) of one modulus in two buffers [320,368) and [368,416);
+// the eight Phase-A slots reuse [0,384).  FP16 carrier: two accumulator sets
+// [0,128) and [128,256), two A buffers from column 320, Phase-A slots
+// [128,512).  One pipeline step per modulus: its MMAs run while the next
 // modulus' digits are generated.
 // ---------------------------------------------------------------------------
 constexpr int FP8_WARPS = 16;
@@ -455,12 +457,13 @@ __global__ void __launch_bounds__(FP8_WARPS * 32, 1)
     uint8_t *sIn = sStage;
     __shared__ int64_t s_e0;  // stage 1: first element of the input tile
     (void)gmc;
-    // Thread 32 issues every bulk copy into shared memory; on the failure path
-    // it waits (bounded) for the last copy into each barrier before the CTA
-    // exits.  Kept in shared memory (written and read by thread 32 only, so no
-    // registers are held through the pipeline): the last modulus whose
-    // constants went into B buffer 0 / 1, and whether the Phase-A constants
-    // were requested.
+    // Thread 32 issues every bulk copy of constants (and, in stage 1, of the
+    // input tile; stage 2's input copies come from warps 4..7 and complete on
+    // the same barrier); on the failure path it waits (bounded) for the last
+    // copy into each barrier before the CTA exits.  Kept in shared memory
+    // (written and read by thread 32 only, so no registers are held through
+    // the pipeline): the last modulus whose constants went into B buffer 0 /
+    // 1, and whether the Phase-A constants were requested.
     __shared__ int pf_last[3];
     if (w == 0) {
         tmem_alloc(smem_u32(&tmem_holder), 512);
