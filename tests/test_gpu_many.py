@@ -179,3 +179,44 @@ def test_default_tuning_reported_and_exact(mode):
         want = oracle_full(xs[i].cpu().numpy(), tuple(sp), -1)
         assert bits_equal(outs[i].cpu().numpy(), want), d
     pm.close()
+
+
+def test_uneven_batch_40_grids_dd_spot_outputs():
+    """The 40-grid uneven batch as bench.py times it (16 x 64^3, 12 x
+    96x128x128, 8 x 192^3, 4 x 256x256x384, N(0,1) inputs, default tuning),
+    FP8 mode, against the oracle's double-double 3-D DFT at eight sampled
+    outputs of the first grid of every size: the normwise error over each
+    size's samples is below 1e-14 and at most twice the native FP64 kernel's
+    on the same grid."""
+    from oracle import ref
+    from paper_2606_23698_gb300 import Plan, PlanMany
+    dims = S.UNEVEN_BATCH
+    xs = [S.complex_gaussian(S.SEED_UNEVEN + i, d, device="cuda") for i, d in enumerate(dims)]
+    pm = PlanMany(dims, mode="fp8")
+    outs = pm.exec(xs, dir=-1)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(40)
+    firsts = {}
+    for i, d in enumerate(dims):
+        firsts.setdefault(d, i)
+    for d, i in firsts.items():
+        spots = [(0, 0, 0)] + [tuple(int(rng.integers(0, n)) for n in d) for _ in range(7)]
+        nat = Plan(*d, mode="fp64")
+        yn = nat.exec(xs[i], dir=-1)
+        torch.cuda.synchronize()
+        y8 = outs[i].reshape(d)
+        yn = yn.reshape(d)
+        got = {"fp8": np.array([complex(y8[k].item()) for k in spots]),
+               "fp64": np.array([complex(yn[k].item()) for k in spots])}
+        nat.close()
+        xh = xs[i].cpu().numpy().reshape(d)
+        dd = np.array([ref.dft3d_dd_point(xh, k) for k in spots])
+        errs = {}
+        for mode, y in got.items():
+            dr = (y.real - dd[:, 0]) - dd[:, 1]
+            di = (y.imag - dd[:, 2]) - dd[:, 3]
+            errs[mode] = float(np.sqrt(np.sum(dr * dr + di * di) / np.sum(dd[:, 0] ** 2 + dd[:, 2] ** 2)))
+        print(d, "sampled normwise error vs double-double:", errs)
+        assert errs["fp8"] < 1e-14 and errs["fp64"] < 1e-14, (d, errs)
+        assert errs["fp8"] <= 2 * errs["fp64"], (d, errs)
+    pm.close()
