@@ -157,7 +157,7 @@ __device__ __forceinline__ void copy_input_tile32(const InputTile32 &t, const fl
                                                   int lane) {
     if (lane == 0) mbar_expect_tx(mbar, (uint32_t)((t.e1 - t.e0) * 8));
     __syncwarp();
-    const int64_t chunk = 512;  // elements (4 KB) per copy
+    const int64_t chunk = 4096;  // elements (32 KB, a whole tile) per copy
     for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
         tma_bulk_g2s(smem_u32(sIn + (e - t.e0) * 8), in + e, (uint32_t)(min(chunk, t.e1 - e) * 8), mbar);
 }
@@ -176,7 +176,7 @@ __device__ __forceinline__ void load_input_tile32(const ColMapT &map, const Inpu
 }
 // Stage 1: L2 prefetch of an input tile (warp-wide call)
 __device__ __forceinline__ void prefetch_input_tile32(const InputTile32 &t, const float2 *in, int lane) {
-    const int64_t chunk = 512;
+    const int64_t chunk = 4096;
     for (int64_t e = t.e0 + (int64_t)lane * chunk; e < t.e1; e += 32 * chunk)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + e), "r"((uint32_t)(min(chunk, t.e1 - e) * 8))
                      : "memory");
@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
     const uint8_t *gplanes = planes + (size_t)group * NMOD32 * BUF_PLANES * PLANE_B;
     uint8_t *sIn = sStage;  // the input tile sits in the staging until every thread has read it
     __shared__ int64_t s_e0;
+    __shared__ int64_t s_pf_src0;  // stage 2: the tile one wave ahead (first column's element; valid columns)
+    __shared__ int s_pf_nvalid;
 
     if (w == 0) {
         tmem_alloc(smem_u32(&tmem_holder), 512);
@@ -269,8 +271,15 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         }
     } else if (w == 2) {
         const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
-        if (tma_in && map.stage == 1 && pf_ahead > 0 && nb < (int64_t)gridDim.x)
+        const bool pf = pf_ahead > 0 && nb < (int64_t)gridDim.x;
+        if (tma_in && map.stage == 1 && pf) {
             prefetch_input_tile32(input_tile32(map, ncols, nb * TILE, TILE), in, lane);
+        } else if (map.stage == 2 && lane == 0) {
+            // stage 2 prefetches after the deconstruction (below)
+            const InputTile32 pt = pf ? input_tile32(map, ncols, nb * TILE, TILE) : InputTile32{0, 0, 0, 0, 0};
+            s_pf_src0 = pt.src0;
+            s_pf_nvalid = pt.nvalid;
+        }
     } else if (w >= 4 && w < 8 && tma_in && map.stage == 2) {
         // stage 2: one bulk copy per column (K elements of one line), issued
         // by four warps once warp 1 has set up the barrier (as in the FP8
@@ -436,14 +445,11 @@ __global__ void __launch_bounds__(F32_WARPS * 32, 1)
         // stage 2: the tile one wave of CTAs ahead into L2 by plain prefetches
         // after the deconstruction, one 128-byte line per thread (as in the
         // FP8 stage kernel)
-        const int64_t nb = (int64_t)blockIdx.x + pf_ahead;
-        if (pf_ahead > 0 && nb < (int64_t)gridDim.x) {
-            const InputTile32 pt = input_tile32(map, ncols, nb * TILE, TILE);
-            const int lpr = (K * 8 + 127) / 128;
-            for (int r = tid; r < pt.nvalid * lpr; r += F32_WARPS * 32) {
-                const int i = r / lpr, q = r - i * lpr;
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(in + pt.src0 + (int64_t)i * pt.n) + q * 128));
-            }
+        const int lpr = (K * 8 + 127) / 128;
+        const int64_t src0 = s_pf_src0;
+        for (int r = tid; r < s_pf_nvalid * lpr; r += F32_WARPS * 32) {
+            const int i = r / lpr, q = r - i * lpr;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(in + src0 + (int64_t)i * map.n) + q * 128));
         }
     }
     gen(0);
