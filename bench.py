@@ -239,9 +239,9 @@ def fp32_variant(torch, Plan, x, y64, stream):
                 "algorithmic": "218 integer instructions per complex output (paper c_epi = 109 per scalar)",
                 "hbm_frac_of_measured": (16 * N3 / (kms * 1e-3) / 1e9) / peaks.get("hbm_gbs", 6791.0),
                 # one ncu capture of the same kernel on 16 x 1024 x 1024 complex64
-                # (128 MiB in and out): dram read 134,393,600 + write 89,574,656 bytes,
+                # (128 MiB in and out): dram read 134,399,744 + write 89,726,208 bytes,
                 # scaled by the 64 times more columns of a 1024^3 launch
-                "traffic": (134393600 + 89574656) * 64 if N3 == 1024 ** 3 else None}
+                "traffic": (134399744 + 89726208) * 64 if N3 == 1024 ** 3 else None}
             del scratch
         out[m] = res
         pl.close()
@@ -601,9 +601,9 @@ def main():
     fp8_ops = 2 * N3 * (228 * 32 + 32 * 48)
     # DRAM bytes per FP8 stage launch at 1024^3 from one ncu capture of the same
     # kernel on a 16 x 1024 x 1024 grid (256 MiB in and out, above L2):
-    # dram__bytes_read.sum 268,655,616 + dram__bytes_write.sum 223,062,016,
+    # dram__bytes_read.sum 268,645,376 + dram__bytes_write.sum 223,128,320,
     # scaled by the 64 times more columns of a 1024^3 launch
-    traffic = (268655616 + 223062016) * 64 if (mode == "fp8" and n == 1024) else None
+    traffic = (268645376 + 223128320) * 64 if (mode == "fp8" and n == 1024) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tinst/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "kernel": f"stage_{mode}_kernel (axis 2, stage 1)", "kernel_ms": kern_ms,
