@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
                                                               ColMap map, int64_t ncols, int K,
                                                               int Kout,
                                                               const double2 *__restrict__ in,
-                                                              double2 *__restrict__ out, DebugDump dbg) {
+                                                              double2 *__restrict__ out, int64_t pf_cols,
+                                                              DebugDump dbg) {
     constexpr bool PK = KPAD == 16;         // b0 and b1 limbs in one k32 block
     constexpr int KB = PK ? 1 : KPAD / 32;  // k32 blocks of data elements
     constexpr int KB2 = PK ? 1 : 2 * KB;    // limb GEMM blocks (b0 limbs then b1 limbs)
@@ -93,6 +94,17 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
 
     for (int i = threadIdx.x; i < (int)(sizeof(ModConsts) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t *>(&mc)[i] = reinterpret_cast<const uint32_t *>(gmc)[i];
+    if (map.stage == 1 && pf_cols > 0 && c0 + pf_cols < ncols) {
+        // stage 1: the input of the CTA one wave ahead (whole lines, one
+        // contiguous range) into L2, one 128-byte line per thread; 2 % per
+        // stage-1 launch.  Stage 2's columns are pieces of separate lines, and
+        // the same prefetch cost it more than it saved.
+        const int64_t cn = c0 + pf_cols;
+        const int64_t e0 = (cn / map.p) * map.n;
+        const int64_t e1 = (min(cn + CT_COLS - 1, ncols - 1) / map.p + 1) * map.n;
+        for (int64_t off = (int64_t)threadIdx.x * 8; e0 + off < e1; off += (int64_t)blockDim.x * 8)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(in + e0 + off));
+    }
 
     // ---------------- phase 1: deconstruct this lane's column elements -------------
     const int col_local = gi * 8 + grp;
@@ -292,6 +304,14 @@ static cudaError_t launch_t(const AxisTables &t, const ModConsts *dmc, const Col
     if (err != cudaSuccess) return err;
     int64_t blocks = (ncols + CT_COLS - 1) / CT_COLS;
     if (blocks == 0) return cudaSuccess;
+    // columns one wave of CTAs ahead (resident CTAs per SM x SMs), for the
+    // stage-1 L2 prefetch
+    int dev = 0, nsm = 0, per_sm = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128 * MT, smem);
+    if (err != cudaSuccess) return err;
+    const int64_t pf_cols = (int64_t)nsm * per_sm * CT_COLS;
     DebugDump d;
     if (dbg) {
         d = *dbg;
@@ -299,7 +319,8 @@ static cudaError_t launch_t(const AxisTables &t, const ModConsts *dmc, const Col
         d.L = map.L;
         d.Lpad = map.Lpad;
     }
-    kern<<<(unsigned)blocks, 128 * MT, smem, s>>>((const uint4 *)table, dmc, map, ncols, K, Kout, in, out, d);
+    kern<<<(unsigned)blocks, 128 * MT, smem, s>>>((const uint4 *)table, dmc, map, ncols, K, Kout, in, out, pf_cols,
+                                                   d);
     return cudaGetLastError();
 }
 
