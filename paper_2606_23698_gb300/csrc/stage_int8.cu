@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
     uint2 *sB = reinterpret_cast<uint2 *>(smem_raw);
     __shared__ ModConsts mc;
     __shared__ int colexp[CT_COLS];
+    __shared__ int64_t s_pf_src;  // stage 2: first element of the CTA one wave ahead (-1: none)
+    __shared__ int s_pf_nv;       // and its valid columns
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gi = warp & 3, sub = warp >> 2;
@@ -94,11 +96,21 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
 
     for (int i = threadIdx.x; i < (int)(sizeof(ModConsts) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t *>(&mc)[i] = reinterpret_cast<const uint32_t *>(gmc)[i];
+    if (map.stage == 2 && threadIdx.x == 0) {
+        const int64_t cn = c0 + pf_cols;
+        s_pf_src = -1;
+        if (pf_cols > 0 && cn < ncols) {
+            const int64_t k2 = cn / map.Lpad, l0 = cn - k2 * map.Lpad;
+            s_pf_src = l0 < map.L ? l0 * map.n + k2 * map.p : -1;
+            s_pf_nv = (int)min((int64_t)CT_COLS, map.L - l0);
+        }
+    }
     if (map.stage == 1 && pf_cols > 0 && c0 + pf_cols < ncols) {
         // stage 1: the input of the CTA one wave ahead (whole lines, one
-        // contiguous range) into L2, one 128-byte line per thread; 2 % per
-        // stage-1 launch.  Stage 2's columns are pieces of separate lines, and
-        // the same prefetch cost it more than it saved.
+        // contiguous range) into L2, one 128-byte line per thread (6 % per
+        // stage-1 launch).  Stage 2 prefetches after the set-up barrier, from
+        // a target thread 0 found once (per-thread target arithmetic there
+        // cost more than the prefetch saved).
         const int64_t cn = c0 + pf_cols;
         const int64_t e0 = (cn / map.p) * map.n;
         const int64_t e1 = (min(cn + CT_COLS - 1, ncols - 1) / map.p + 1) * map.n;
@@ -134,6 +146,14 @@ __global__ void __launch_bounds__(128 * MT) stage_int8_kernel(const uint4 *__res
     const int64_t drow = DBG && cvalid ? dbg.row(c) : -1;
     if (DBG && drow >= 0 && sub == 0 && tig == 0) dbg.e[drow] = e;
     __syncthreads();  // mc ready
+    if (map.stage == 2 && s_pf_src >= 0) {
+        // stage 2: the CTA one wave ahead (its columns' K-element pieces)
+        const int lpr = (K * 16 + 127) / 128;
+        for (int r = threadIdx.x; r < s_pf_nv * lpr; r += blockDim.x) {
+            const int i = r / lpr, q = r - i * lpr;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(in + s_pf_src + (int64_t)i * map.n) + q * 128));
+        }
+    }
 
 #pragma unroll
     for (int kb = 0; kb < KB; kb++) {
