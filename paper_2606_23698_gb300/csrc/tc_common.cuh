@@ -30,13 +30,6 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N, uint32_t fmt = 0
            ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void tc_mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 __device__ __forceinline__ void tc_mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                            uint32_t acc) {
     asm volatile(
@@ -204,15 +197,6 @@ __device__ __forceinline__ uint32_t f16x2(float lo, float hi) {
     uint32_t r;
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
-}
-
-// round-to-nearest-even integer of |x| < 2^22 in FP32 (magic-number add)
-__device__ __forceinline__ float rint_small(float x) {
-    return __fadd_rn(__fadd_rn(x, 12582912.0f), -12582912.0f);
-}
-// RNE integer of a * b + c for |a b + c| < 2^22 (fused, one rounding before the magic add)
-__device__ __forceinline__ float rint_fma(float a, float b, float c) {
-    return __fadd_rn(__fmaf_rn(a, b, c + 12582912.0f), -12582912.0f);
 }
 
 // Packed two-lane FP32 arithmetic (one instruction for both lanes).
